@@ -1,0 +1,288 @@
+"""Benchmark: seconds per CS decomposition (and TFLOP/s) at n = 4096, FP64.
+
+Workload: real FP64 CSD of a 2n x n matrix with orthonormal columns, n = 4096,
+theta half uniform on [0, pi/2], a quarter within 1e-8 of 0 and a quarter
+within 1e-8 of pi/2, plus an additive 1e-14 Gaussian perturbation and
+re-orthonormalisation (kappa(A_i) ~ 1e8 and beyond).  One step = one full
+csd_polar call (two Zolo-pd polar decompositions, Zolo-eig of B = H2 - H1,
+assembly of U1, U2, V1, theta) on device-resident inputs.  Throughput in
+TFLOP/s counts the paper's 198 n^3 flops per CSD (Section 3, remark (v):
+67 (m1 + m2) n^2 + 64 n^3 with m1 = m2 = n).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank decomposes its own instance (replicas; the
+path has no exchange step), value = total time / total CSDs.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_CSD = lambda n: 198.0 * n ** 3
+U = 2.0 ** -53
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-n", type=int, default=512, help="oracle sample size for the CPU baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp64_alu_peak_tflops():
+    """FP64 FMA pipe peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x
+    2 flop x 2070 MHz = 1.2586 TFLOP/s (our DFMA microbenchmark measured
+    1.195 TFLOP/s at 1995 MHz, i.e. 2.0 DFMA/clk/SM)."""
+    return 152 * 2 * 2 * 2070e6 / 1e12
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, rank, ws):
+    """Reference arm: the CPU FP64 oracle (Jacobi SVD polar + cyclic Jacobi
+    eig, OpenMP) on a bounded sample -- an instance of the same recipe at
+    n = sample_n -- scaled to n by (n / sample_n)^3."""
+    if rank != 0:
+        return
+    from oracle import csd as O
+    from oracle import jacobi as OJ
+    from paper_1804_09002_gb300 import inputs as I
+    ns = args.sample_n
+    A1, A2, _ = I.clustered_csd(ns, seed=2)
+    for _ in range(args.warmup):
+        O.csd(A1, A2)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.csd(A1, A2)
+        ts.append(time.perf_counter() - t0)
+    scale = (args.n / ns) ** 3
+    t = statistics.median(ts) * scale
+    line = {
+        "impl": "reference", "metric": "s/CSD at n=4096 (FP64)", "value": t, "unit": "s/CSD",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "tflops": FLOPS_PER_CSD(args.n) / t / 1e12,
+        "config": {"workload": f"real FP64 CSD n={args.n}, clustered theta, 1e-14 noise, re-orthonormalised",
+                   "n": args.n, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": t, "unit": "s/CSD", "cores": OJ.threads(), "kind": "oracle",
+                         "sample": f"oracle CSD of an n={ns} instance of the same recipe, median of {args.steps}, "
+                                   f"scaled by (n/{ns})^3"},
+        "e2e": {"value": t, "unit": "s/CSD", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args):
+    from oracle import csd as O
+    from oracle import jacobi as OJ
+    from paper_1804_09002_gb300 import inputs as I
+    ns = args.sample_n
+    A1, A2, _ = I.clustered_csd(ns, seed=2)
+    t0 = time.perf_counter()
+    O.csd(A1, A2)
+    t = time.perf_counter() - t0
+    return {"value": t * (args.n / ns) ** 3, "unit": "s/CSD", "cores": OJ.threads(), "kind": "oracle",
+            "sample": f"oracle CSD of one n={ns} instance of the same recipe ({t:.2f} s), scaled by (n/{ns})^3"}
+
+
+def main():
+    args = parse()
+    dist, rank, ws, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        if dist:
+            dist.destroy_process_group()
+        return
+    import torch
+    from paper_1804_09002_gb300 import binding as B
+    from paper_1804_09002_gb300 import inputs as I
+
+    # the CPU baseline runs the oracle in worker threads: do it before the
+    # first GPU call (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n = args.n
+    A1h, A2h, th_known = I.clustered_csd(n, seed=2 + rank)
+    colmaj = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).to(dev).t()
+    A1, A2 = colmaj(A1h), colmaj(A2h)
+    ctx = B.Context(local)
+    out = {k: torch.empty((n, n), dtype=torch.float64, device=dev).t() for k in ("U1", "U2", "V1")}
+    out["theta"] = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def step():
+        return ctx.csd_polar(A1, A2, out=out)
+
+    for _ in range(args.warmup):
+        R = step()
+    torch.cuda.synchronize()
+    # ---- timed region (device-resident inputs; A1, A2 = 256 MiB > L2)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    B.lib.csd_profile_enable(ctx._h, 1)
+    launches0 = B.lib.csd_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        R = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    launches = B.lib.csd_launch_count() - launches0
+    prof = B.csd_profile()
+    B.lib.csd_profile_read(ctx._h, prof)
+    B.lib.csd_profile_enable(ctx._h, 0)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    s_per_csd = ms / 1e3 / (args.steps * ws)
+    # ---- accuracy of the last result (torch on the GPU, not the oracle)
+    rk = R["rank"]
+    th = R["theta"][:rk]
+    c, s_ = torch.cos(th), torch.sin(th)
+    U1, U2, V1 = (R[k][:, :rk] for k in ("U1", "U2", "V1"))
+    num = torch.sqrt(torch.linalg.norm(A1 - (U1 * c) @ V1.T) ** 2 + torch.linalg.norm(A2 - (U2 * s_) @ V1.T) ** 2)
+    bwd = float(num / np.sqrt(2.0 * n))  # ||A||_F = sqrt(n) per block for orthonormal columns
+    ang = float(np.max(np.abs(th.cpu().numpy() - th_known)))
+    orth = max(float(torch.linalg.norm(X.T @ X - torch.eye(rk, device=dev, dtype=X.dtype), 2)) for X in (U1, U2, V1))
+    # ---- e2e: same call with pinned host buffers (copies inside the call)
+    e2e = None
+    if args.e2e_steps > 0:
+        A1p = torch.from_numpy(np.ascontiguousarray(A1h.T)).pin_memory().t()
+        A2p = torch.from_numpy(np.ascontiguousarray(A2h.T)).pin_memory().t()
+        outp = {k: torch.empty((n, n), dtype=torch.float64).pin_memory().t() for k in ("U1", "U2", "V1")}
+        outp["theta"] = torch.empty(n, dtype=torch.float64).pin_memory()
+        ctx.csd_polar(A1p, A2p, out=outp)  # warm the host-buffer path
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.csd_polar(A1p, A2p, out=outp)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": te, "unit": "s/CSD", "h2d_bytes_per_step": 2 * n * n * 8,
+               "d2h_bytes_per_step": 3 * n * n * 8 + n * 8}
+    # ---- roofline of the dominant kernel (GEMM on the FP64 FMA pipe)
+    kinds = ["gemm", "qr_panel", "potrf", "jacobi"]
+    kms = {k: prof.ms[i] for i, k in enumerate(kinds)}
+    dom = max(range(4), key=lambda i: prof.ms[i])
+    avg_ms = prof.ms[dom] / max(prof.count[dom], 1)
+    flops_per_launch = prof.flops[dom] / max(prof.count[dom], 1)
+    peak = fp64_alu_peak_tflops()
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+    line = {
+        "metric": "s/CSD at n=4096 (FP64)", "value": s_per_csd, "unit": "s/CSD", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "tflops": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12,
+        "tflops_frac_of_fp64_peak": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12 / peak,
+        "config": {"workload": f"real FP64 CSD n={n}, clustered theta (1/2 uniform, 1/4 within 1e-8 of 0, "
+                               f"1/4 within 1e-8 of pi/2), 1e-14 noise, re-orthonormalised",
+                   "n": n, "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (2 x 128 MiB)"},
+        "accuracy": {"max_abs_theta_err_vs_known": ang, "backward_err_fro_over_u": bwd / U,
+                     "orth_over_u": orth / U, "rank": rk},
+        "roofline": {"kernel": kinds[dom], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"},
+        "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "clocks": ck, "gpu_launches": int(launches),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

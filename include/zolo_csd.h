@@ -1,0 +1,153 @@
+/*
+ * zolo_csd.h -- C ABI of the GB300 (sm_103a) Zolo-csd library.
+ *
+ * The library computes the CS decomposition of a 2n x n partial isometry
+ * A = [A1; A2] (Section 1; Theorem 2.1 for the rank-deficient case) by the
+ * method of Algorithm 1: two polar decompositions A_i = W_i H_i by Zolo-pd
+ * (Section 5), the eigendecomposition of B = H2 - H1 + mu (I - A^*A)
+ * (Section 3, line 4 of Algorithm 1) by the spectral divide-and-conquer
+ * Zolo-eig (Section 5), and U_i = W_i V1, C/S = diag(V1^* H_i V1),
+ * theta = atan2(S, C) (Algorithm 1 lines 6-9, remark (iii)).  Ill-conditioned
+ * blocks use the eps-modified Zolo-pd with eps = 1e-15 and, when W_i is not
+ * orthonormal, Algorithm 2; rank-deficient inputs use Algorithm 3.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major with leading dimension ld >= n.
+ *   - dtype 0 = real FP64 (double), dtype 1 = complex FP64 (two doubles,
+ *     real part first, C99 double complex layout).
+ *   - Matrix and vector pointers may point to device memory or to host
+ *     memory (pageable or pinned); the library inspects each pointer, stages
+ *     host data through its own device buffers and copies results back.
+ *   - The caller owns all input and output buffers; inputs are never
+ *     modified.  The library owns its device workspace, which lives in the
+ *     context, grows on demand and is released by csd_destroy.
+ *   - Work is issued on the context's CUDA stream; on return all outputs are
+ *     complete (the call synchronises the stream).
+ *   - Return value: 0 on success; -k when argument k (1-based) is invalid;
+ *     a positive CSD_ERR_* / CSD_WARN_* code otherwise (csd_status_str).
+ *     A warning still writes every output.
+ */
+#ifndef ZOLO_CSD_H
+#define ZOLO_CSD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSD_OK 0
+#define CSD_ERR_CUDA 1            /* a CUDA call failed (context may be lost) */
+#define CSD_ERR_NOT_CONVERGED 2   /* Zolo-pd iterate did not converge */
+#define CSD_WARN_ALG2_RCHECK 3    /* Algorithm 2: ||R~ - R|| above tolerance (Section 5.1) */
+#define CSD_ERR_EIG_SPLIT 4       /* Zolo-eig could not split a block after retries */
+#define CSD_ERR_NONFINITE 5       /* input holds NaN or Inf */
+#define CSD_ERR_ALLOC 6           /* device workspace allocation failed */
+#define CSD_ERR_INTERNAL 7        /* internal consistency check failed */
+#define CSD_ERR_NO_DEVICE 8       /* no usable CUDA device for the context */
+
+#define CSD_F64 0
+#define CSD_C128 1
+
+typedef struct csd_ctx csd_ctx;
+
+/* Diagnostics filled by every entry point (may be NULL). */
+typedef struct {
+  int status;             /* same as the return value */
+  int rank;               /* detected rank r = round(||A||_F^2) (remark (vi)) */
+  double mu;              /* 0 (full rank) or 2 (Algorithm 3) */
+  int zolo_iters;         /* Zolo-pd iterations per polar decomposition */
+  int r_terms[4];         /* partial-fraction terms r of each iteration */
+  double ell[4];          /* lower end l of [l, 1] entering each iteration */
+  int chol_fallback;      /* Cholesky iterations redone in QR form */
+  int alg2_used[2];       /* Algorithm 2 applied to block i */
+  double orth_err[2];     /* ||W_i^* W_i - I||_F of the Zolo-pd factor */
+  double rdiff[2];        /* ||R~_i - R_i||_F / ||R_i||_F (Algorithm 2 check) */
+  int eig_splits;         /* Zolo-eig splits performed */
+  int eig_retries;        /* splits redone with a perturbed shift */
+  int eig_leaves;         /* leaf blocks solved by Jacobi */
+  double eig_offblock;    /* largest ||B21||_F / ||B||_F accepted at a split */
+  double ms_total;        /* wall time of the call, milliseconds */
+} csd_info;
+
+/* Create a context on CUDA device `device` bound to the CUDA stream
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).  *ctx
+ * receives the handle.  Returns 0, -1/-2 on bad arguments, or
+ * CSD_ERR_NO_DEVICE / CSD_ERR_CUDA. */
+int csd_create(csd_ctx** ctx, int device, void* stream);
+
+/* Rebind the context to another stream of the same device. */
+int csd_set_stream(csd_ctx* ctx, void* stream);
+
+/* Release the context and its device workspace.  NULL is accepted. */
+int csd_destroy(csd_ctx* ctx);
+
+/* Bytes of device workspace currently held by the context. */
+long long csd_workspace_bytes(const csd_ctx* ctx);
+
+/* CS decomposition (Algorithm 1; Algorithms 2 and 3 as needed).
+ *   A1, A2   n x n blocks of A (lda1, lda2 >= n), read only.
+ *   U1, U2   n x n outputs (ldu1, ldu2 >= n): columns 0..rank-1 hold the
+ *            economical factors of Algorithm 3, the rest are unspecified.
+ *   V1       n x n output (ldv1 >= n), same column convention.
+ *   theta    length-n output: theta[0..rank-1] ascending in [0, pi/2]
+ *            (remark (iii)); entries rank..n-1 are set to 0.
+ *   rank     host int, receives r (may be NULL).
+ * A1 = U1 diag(cos theta) V1^*, A2 = U2 diag(sin theta) V1^* up to the
+ * backward error of Theorem 3.1. */
+int csd_polar(csd_ctx* ctx, int dtype, int n,
+              const void* A1, int lda1, const void* A2, int lda2,
+              void* U1, int ldu1, void* U2, int ldu2, void* V1, int ldv1,
+              double* theta, int* rank, csd_info* info);
+
+/* Polar decomposition A = W H by Zolo-pd (Section 5) on [eps, 1],
+ * eps = 1e-15 (Section 5.1), for an n x n A with ||A||_2 <= 1 (as for the
+ * blocks of a partial isometry; larger inputs are scaled by 1/||A||_F first).
+ * W (ldw >= n) receives the unitary factor, H (ldh >= n) the Hermitian
+ * factor sym(W^* A) (H may be NULL). */
+int polar(csd_ctx* ctx, int dtype, int n, const void* A, int lda,
+          void* W, int ldw, void* H, int ldh, csd_info* info);
+
+/* Hermitian eigendecomposition B = V diag(lambda) V^* by Zolo-eig
+ * (Section 5: spectral divide and conquer on the polar factor of B - sI).
+ * Only the Hermitian part (B + B^*)/2 is used.  lambda (length n) receives
+ * the eigenvalues ascending, V (ldv >= n) the eigenvectors. */
+int heig(csd_ctx* ctx, int dtype, int n, const void* B, int ldb,
+         double* lambda, void* V, int ldv, csd_info* info);
+
+/* Zolotarev coefficients for [ell, 1] and r terms (host only, no GPU):
+ * c[0..2r-1] = c_1..c_2r, a[0..r-1] = a_1..a_r, *mhat (Z(1) = 1) and
+ * *ell_next = Z(ell).  0 < ell < 1, 1 <= r <= 16.  Returns 0 or -k. */
+int zolo_coeffs(double ell, int r, double* c, double* a, double* mhat, double* ell_next);
+
+/* Iteration plan of Zolo-pd from ell0 (host only): at each step the
+ * smallest r <= rmax with 1 - ell_next <= 4u, else rmax; stops once
+ * 1 - ell <= 4u.  r_out/ell_out (length max_iter) receive r and the entering
+ * ell of each step; returns the number of steps (or -k). */
+int zolo_plan(double ell0, int rmax, int max_iter, int* r_out, double* ell_out);
+
+/* Kernel accounting, for roofline reports (not needed for computing).
+ * Kinds: 0 = GEMM (FP64 FMA tiles), 1 = Householder QR panel, 2 = Cholesky
+ * diagonal block, 3 = Jacobi leaves.  While enabled, each launch of these
+ * kernels is bracketed by CUDA events on the context stream; `flops` sums
+ * the multiply-add work each launch executes (2 per real FMA, 8 per complex
+ * FMA; QR panel and Cholesky block use their textbook counts).
+ * csd_profile_enable resets the counters; csd_profile_read synchronises the
+ * stream and returns the totals since then. */
+typedef struct {
+  long long count[4];
+  double ms[4];
+  double flops[4];
+} csd_profile;
+
+int csd_profile_enable(csd_ctx* ctx, int enable);
+int csd_profile_read(csd_ctx* ctx, csd_profile* out);
+
+/* Process-wide number of kernels this library has launched so far. */
+long long csd_launch_count(void);
+
+/* Human-readable text of a status code. */
+const char* csd_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZOLO_CSD_H */

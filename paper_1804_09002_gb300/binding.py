@@ -1,0 +1,288 @@
+"""ctypes binding of libzolo_csd.so (include/zolo_csd.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays are column-major.  Accepted inputs are torch tensors
+(CUDA or CPU) and numpy arrays; CUDA tensors are passed by device pointer on
+torch's current stream, host arrays by host pointer (the library stages them
+through device memory itself).  Outputs are allocated like the inputs
+(torch CUDA tensors stay on the device, numpy arrays stay on the host).
+
+There is no fallback: if the shared library is missing or fails to load,
+importing this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libzolo_csd.so")
+
+CSD_F64 = 0
+CSD_C128 = 1
+STATUS_OK = 0
+WARN_ALG2_RCHECK = 3
+
+
+class csd_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("rank", ctypes.c_int),
+        ("mu", ctypes.c_double),
+        ("zolo_iters", ctypes.c_int),
+        ("r_terms", ctypes.c_int * 4),
+        ("ell", ctypes.c_double * 4),
+        ("chol_fallback", ctypes.c_int),
+        ("alg2_used", ctypes.c_int * 2),
+        ("orth_err", ctypes.c_double * 2),
+        ("rdiff", ctypes.c_double * 2),
+        ("eig_splits", ctypes.c_int),
+        ("eig_retries", ctypes.c_int),
+        ("eig_leaves", ctypes.c_int),
+        ("eig_offblock", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+class csd_profile(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4), ("flops", ctypes.c_double * 4)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing; build it with paper_1804_09002_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.csd_create.argtypes = [ctypes.POINTER(vp), ci, vp]
+    lib.csd_set_stream.argtypes = [vp, vp]
+    lib.csd_destroy.argtypes = [vp]
+    lib.csd_workspace_bytes.argtypes = [vp]
+    lib.csd_workspace_bytes.restype = ctypes.c_longlong
+    lib.csd_polar.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, vp, ci, vp, ci, vp,
+                              ctypes.POINTER(ci), ctypes.POINTER(csd_info)]
+    lib.polar.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, ctypes.POINTER(csd_info)]
+    lib.heig.argtypes = [vp, ci, ci, vp, ci, vp, vp, ci, ctypes.POINTER(csd_info)]
+    lib.zolo_coeffs.argtypes = [cd, ci, vp, vp, ctypes.POINTER(cd), ctypes.POINTER(cd)]
+    lib.zolo_plan.argtypes = [cd, ci, ci, vp, vp]
+    lib.csd_profile_enable.argtypes = [vp, ci]
+    lib.csd_profile_read.argtypes = [vp, ctypes.POINTER(csd_profile)]
+    lib.csd_launch_count.argtypes = []
+    lib.csd_launch_count.restype = ctypes.c_longlong
+    lib.csd_status_str.argtypes = [ci]
+    lib.csd_status_str.restype = ctypes.c_char_p
+    for f in ("csd_create", "csd_set_stream", "csd_destroy", "csd_polar", "polar", "heig", "zolo_coeffs",
+              "zolo_plan", "csd_profile_enable", "csd_profile_read"):
+        getattr(lib, f).restype = ci
+    return lib
+
+
+lib = _load()
+
+EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes", "csd_polar", "polar", "heig",
+            "zolo_coeffs", "zolo_plan", "csd_status_str", "csd_profile_enable", "csd_profile_read",
+            "csd_launch_count"]
+
+
+class CSDError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"{where}: status {status} ({lib.csd_status_str(status).decode()})")
+        self.status = status
+
+
+# ------------------------------------------------------------------ host-only
+def zolo_coeffs(ell, r):
+    """Zolotarev coefficients computed by the library's host code:
+    (c[2r], a[r], mhat, ell_next)."""
+    c = np.zeros(2 * r)
+    a = np.zeros(r)
+    m = ctypes.c_double()
+    en = ctypes.c_double()
+    st = lib.zolo_coeffs(float(ell), int(r), c.ctypes.data, a.ctypes.data, ctypes.byref(m), ctypes.byref(en))
+    if st != 0:
+        raise CSDError(st, "zolo_coeffs")
+    return c, a, m.value, en.value
+
+
+def zolo_plan(ell0=1e-15, rmax=8, max_iter=4):
+    r = np.zeros(max_iter, dtype=np.int32)
+    ell = np.zeros(max_iter)
+    k = lib.zolo_plan(float(ell0), int(rmax), int(max_iter), r.ctypes.data, ell.ctypes.data)
+    if k < 0:
+        raise CSDError(k, "zolo_plan")
+    return r[:k].tolist(), ell[:k].tolist()
+
+
+# ------------------------------------------------------------------ arrays
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x):
+    try:
+        import torch
+    except ImportError:
+        return False
+    return isinstance(x, torch.Tensor)
+
+
+def _dtype_code(x):
+    if _is_torch(x):
+        torch = _torch()
+        if x.dtype == torch.float64:
+            return CSD_F64
+        if x.dtype == torch.complex128:
+            return CSD_C128
+    else:
+        if x.dtype == np.float64:
+            return CSD_F64
+        if x.dtype == np.complex128:
+            return CSD_C128
+    raise TypeError("inputs must be float64 or complex128")
+
+
+def _colmajor(x):
+    """(array, pointer, ld) of a column-major view of the 2-D array x."""
+    if _is_torch(x):
+        if x.dim() != 2:
+            raise ValueError("expected a 2-D tensor")
+        m, n = x.shape
+        if not (x.stride(0) == 1 and x.stride(1) >= max(m, 1)):
+            x = x.t().contiguous().t()
+        return x, x.data_ptr(), max(x.stride(1), 1)
+    x = np.asfortranarray(x)
+    if x.ndim != 2:
+        raise ValueError("expected a 2-D array")
+    return x, x.ctypes.data, max(x.strides[1] // x.itemsize, 1)
+
+
+def _empty_like2(x, m, n, dtype=None):
+    if _is_torch(x):
+        torch = _torch()
+        t = torch.empty((n, m), dtype=dtype or x.dtype, device=x.device).t()
+        return t
+    return np.empty((m, n), dtype=dtype or x.dtype, order="F")
+
+
+def _empty_vec(x, n):
+    if _is_torch(x):
+        torch = _torch()
+        return torch.empty(n, dtype=torch.float64, device=x.device)
+    return np.empty(n, dtype=np.float64)
+
+
+def _ptr(v):
+    return v.data_ptr() if _is_torch(v) else v.ctypes.data
+
+
+class Context:
+    """A library context: device workspace plus the CUDA stream it issues on."""
+
+    def __init__(self, device=0):
+        self._h = ctypes.c_void_p()
+        st = lib.csd_create(ctypes.byref(self._h), int(device), None)
+        if st != 0:
+            raise CSDError(st, "csd_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib.csd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self, x):
+        if _is_torch(x) and x.is_cuda:
+            torch = _torch()
+            lib.csd_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream))
+        else:
+            lib.csd_set_stream(self._h, None)
+
+    def workspace_bytes(self):
+        return lib.csd_workspace_bytes(self._h)
+
+    def csd_polar(self, A1, A2, out=None):
+        """CS decomposition of [A1; A2].  Returns dict(U1, U2, V1, theta,
+        rank, info); columns/entries beyond `rank` are unspecified/zero."""
+        dt = _dtype_code(A1)
+        if _dtype_code(A2) != dt:
+            raise TypeError("A1 and A2 must share a dtype")
+        A1, p1, l1 = _colmajor(A1)
+        A2, p2, l2 = _colmajor(A2)
+        n = A1.shape[1]
+        if tuple(A1.shape) != (n, n) or tuple(A2.shape) != (n, n):
+            raise ValueError("A1 and A2 must be n x n")
+        if out is None:
+            out = dict(U1=_empty_like2(A1, n, n), U2=_empty_like2(A1, n, n), V1=_empty_like2(A1, n, n),
+                       theta=_empty_vec(A1, n))
+        U1, pu1, lu1 = _colmajor(out["U1"])
+        U2, pu2, lu2 = _colmajor(out["U2"])
+        V1, pv1, lv1 = _colmajor(out["V1"])
+        theta = out["theta"]
+        rank = ctypes.c_int()
+        info = csd_info()
+        self._bind_stream(A1)
+        st = lib.csd_polar(self._h, dt, n, p1, l1, p2, l2, pu1, lu1, pu2, lu2, pv1, lv1, _ptr(theta),
+                           ctypes.byref(rank), ctypes.byref(info))
+        if st not in (STATUS_OK, WARN_ALG2_RCHECK):
+            raise CSDError(st, "csd_polar")
+        return dict(U1=U1, U2=U2, V1=V1, theta=theta, rank=rank.value, info=info.as_dict(), status=st)
+
+    def polar(self, A, want_h=True):
+        dt = _dtype_code(A)
+        A, pa, la = _colmajor(A)
+        n = A.shape[1]
+        W = _empty_like2(A, n, n)
+        H = _empty_like2(A, n, n) if want_h else None
+        info = csd_info()
+        self._bind_stream(A)
+        st = lib.polar(self._h, dt, n, pa, la, _ptr(W), n, _ptr(H) if want_h else None, n, ctypes.byref(info))
+        if st != STATUS_OK:
+            raise CSDError(st, "polar")
+        return W, H, info.as_dict()
+
+    def heig(self, B):
+        dt = _dtype_code(B)
+        B, pb, lb = _colmajor(B)
+        n = B.shape[1]
+        V = _empty_like2(B, n, n)
+        lam = _empty_vec(B, n)
+        info = csd_info()
+        self._bind_stream(B)
+        st = lib.heig(self._h, dt, n, pb, lb, _ptr(lam), _ptr(V), n, ctypes.byref(info))
+        if st != STATUS_OK:
+            raise CSDError(st, "heig")
+        return lam, V, info.as_dict()
+
+
+_default = {}
+
+
+def default_context(device=0):
+    if device not in _default:
+        _default[device] = Context(device)
+    return _default[device]
+
+
+def csd_polar(A1, A2, device=0):
+    return default_context(device).csd_polar(A1, A2)
+
+
+def polar(A, device=0, want_h=True):
+    return default_context(device).polar(A, want_h)
+
+
+def heig(B, device=0):
+    return default_context(device).heig(B)

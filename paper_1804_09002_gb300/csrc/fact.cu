@@ -1,0 +1,412 @@
+// Factorization kernels: Householder QR panel (with the compact-WY T factor),
+// Cholesky of a diagonal block with its triangular inverse, and the cyclic
+// Jacobi eigensolver for the small leaf blocks of Zolo-eig.
+//
+// The panel and diagonal-block kernels run one CTA per problem of a batch;
+// everything with O(n^3) work around them is a GEMM (blas.cu).
+#include <algorithm>
+
+#include "ops.h"
+
+namespace zcsd {
+
+namespace {
+
+constexpr int PANEL_THREADS = 512;
+constexpr int PANEL_MAXNB = 32;
+
+// Sum `cnt` per-thread values across the CTA; result in red[nwarps*MAXNB + c].
+// The loop over c is fully unrolled so that `vals` stays in registers.
+template <class T>
+__device__ void block_reduce_vec(T (&vals)[PANEL_MAXNB], int cnt, T* red /* [nwarps+1][PANEL_MAXNB] */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < PANEL_MAXNB; ++c) {
+    if (c < cnt) {
+      double x = re(vals[c]), y = im(vals[c]);
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        if constexpr (sizeof(T) != sizeof(double)) y += __shfl_down_sync(0xffffffffu, y, o);
+      }
+      if (lane == 0) {
+        T v;
+        if constexpr (sizeof(T) == sizeof(double)) v = from_re<T>(x);
+        else { z64 z{x, y}; v = *reinterpret_cast<T*>(&z); }
+        red[w * PANEL_MAXNB + c] = v;
+      }
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < cnt) {
+    T s = zero<T>();
+    for (int i = 0; i < nw; ++i) s = add(s, red[i * PANEL_MAXNB + threadIdx.x]);
+    red[(nw)*PANEL_MAXNB + threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+template <class T>
+__device__ inline T make_c(double x, double y) {
+  if constexpr (sizeof(T) == sizeof(double)) return from_re<T>(x);
+  else { z64 z{x, y}; return *reinterpret_cast<T*>(&z); }
+}
+
+// Householder QR of columns [k0, k0+nb) of M (LAPACK geqr2 + larft semantics):
+// H_k = I - tau_k v_k v_k^*, beta real, A = Q R with Q = H_k0 ... H_k0+nb-1,
+// and Q = I - V T V^* with T upper triangular.
+template <class T>
+__global__ void __launch_bounds__(PANEL_THREADS) qr_panel_kernel(int m, int n, int band, T* Mall, int ldm,
+                                                                 long long sM, int k0, int nb, T* Yall, int ldy,
+                                                                 long long sY, T* Tall, long long sT) {
+  __shared__ T red[(PANEL_THREADS / 32 + 1) * PANEL_MAXNB];
+  __shared__ T wv[PANEL_MAXNB];
+  __shared__ T Ts[PANEL_MAXNB * PANEL_MAXNB];
+  __shared__ T sh_scale, sh_tau, sh_beta;
+  const int b = blockIdx.x;
+  T* M = Mall + b * sM;
+  T* Y = Yall + b * sY;
+  T* Tf = Tall + b * sT;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int hrows = min(m, k0 + nb - 1 + band) - k0;  // rows of the Y panel
+  for (int i = tid; i < PANEL_MAXNB * PANEL_MAXNB; i += nt) Ts[i] = zero<T>();
+  __syncthreads();
+
+  for (int j = 0; j < nb; ++j) {
+    const int k = k0 + j;
+    const int rend = min(m, k + band);
+    // ---- pass 1: d_c = sum_{i>k} conj(M[i,k]) M[i,k0+c] for every panel column c
+    T d[PANEL_MAXNB];
+#pragma unroll
+    for (int c = 0; c < PANEL_MAXNB; ++c) d[c] = zero<T>();
+    for (int i = k + 1 + tid; i < rend; i += nt) {
+      const T x = M[i + (long long)k * ldm];
+#pragma unroll
+      for (int c = 0; c < PANEL_MAXNB; ++c)
+        if (c < nb) d[c] = add(d[c], cmul(x, M[i + (long long)(k0 + c) * ldm]));
+    }
+    block_reduce_vec(d, nb, red);
+    const T* dsum = red + (nt / 32) * PANEL_MAXNB;
+    // ---- reflector (LAPACK larfg) and the dot products it needs
+    if (tid == 0) {
+      const T alpha = M[k + (long long)k * ldm];
+      const double xnorm2 = re(dsum[j]);
+      T tau, scale, beta;
+      if (xnorm2 == 0.0 && im(alpha) == 0.0) {
+        tau = zero<T>();
+        scale = zero<T>();
+        beta = alpha;
+      } else {
+        const double nrm = sqrt(abs2(alpha) + xnorm2);
+        const double bt = re(alpha) >= 0.0 ? -nrm : nrm;
+        beta = from_re<T>(bt);
+        tau = make_c<T>((bt - re(alpha)) / bt, -im(alpha) / bt);
+        scale = div_(from_re<T>(1.0), sub(alpha, beta));
+      }
+      sh_tau = tau;
+      sh_scale = scale;
+      sh_beta = beta;
+    }
+    __syncthreads();
+    const T tau = sh_tau, scale = sh_scale;
+    if (tid < nb) {
+      const int c = tid;
+      const T mk = M[k + (long long)(k0 + c) * ldm];
+      if (c > j) {
+        // w_c = v^* M[:, c] = M[k, c] + conj(scale) d_c
+        wv[c] = add(mk, mul(conj_(scale), dsum[c]));
+      } else if (c < j) {
+        // y_c = V[:, c]^* v = conj(M[k, c]) + scale conj(d_c)
+        wv[c] = add(conj_(mk), mul(scale, conj_(dsum[c])));
+      }
+    }
+    __syncthreads();
+    // T[0:j, j] = -tau T[0:j, 0:j] y[0:j];  T[j, j] = tau
+    if (tid < j) {
+      const int r = tid;
+      T s = zero<T>();
+      for (int c = r; c < j; ++c) s = fmac(Ts[r + c * PANEL_MAXNB], wv[c], s);
+      red[r] = mul(from_re<T>(-1.0), mul(tau, s));  // scratch (red no longer needed)
+    }
+    __syncthreads();
+    if (tid < j) Ts[tid + j * PANEL_MAXNB] = red[tid];
+    if (tid == 0) Ts[j + j * PANEL_MAXNB] = tau;
+    // ---- pass 2: v, Y and the update of the remaining panel columns
+    const T ctau = conj_(tau);
+    for (int i = k + tid; i < rend; i += nt) {
+      T v;
+      if (i == k) v = from_re<T>(1.0);
+      else {
+        v = mul(scale, M[i + (long long)k * ldm]);
+        M[i + (long long)k * ldm] = v;
+      }
+      Y[(i - k0) + (long long)j * ldy] = v;
+      const T cv = mul(ctau, v);
+      for (int c = j + 1; c < nb; ++c) {
+        T* p = M + i + (long long)(k0 + c) * ldm;
+        *p = sub(*p, mul(cv, wv[c]));
+      }
+    }
+    // zeros of the explicit V panel outside [k, rend)
+    for (int i = tid; i < hrows; i += nt) {
+      const int gi = k0 + i;
+      if (gi < k || gi >= rend) Y[i + (long long)j * ldy] = zero<T>();
+    }
+    __syncthreads();
+    if (tid == 0) M[k + (long long)k * ldm] = sh_beta;
+    __syncthreads();
+  }
+  for (int i = tid; i < nb * nb; i += nt) {
+    const int r = i % nb, c = i / nb;
+    Tf[r + c * nb] = Ts[r + c * PANEL_MAXNB];
+  }
+}
+
+constexpr int CHOL_MAXNB = 64;
+
+template <class T>
+__global__ void __launch_bounds__(256) potrf_inv_kernel(int n, T* Aall, int lda, long long sA, int k0, int nb,
+                                                        T* Rall, int ldr, long long sR, int* info) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T(*S)[CHOL_MAXNB + 1] = reinterpret_cast<T(*)[CHOL_MAXNB + 1]>(dyn_smem);
+  T(*X)[CHOL_MAXNB + 1] = S + CHOL_MAXNB;
+  __shared__ int bad;
+  const int b = blockIdx.x;
+  T* A = Aall + b * sA;
+  T* Rinv = Rall + b * sR;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int t = tid; t < nb * nb; t += blockDim.x) {
+    const int i = t % nb, j = t / nb;
+    S[i][j] = (i <= j) ? A[(k0 + i) + (long long)(k0 + j) * lda] : zero<T>();
+    X[i][j] = zero<T>();
+  }
+  __syncthreads();
+  // upper Cholesky, row by row: R[j, j:] from S[j, j:] - sum_{p<j} conj(R[p, j]) R[p, j:]
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      double dd = re(S[j][j]);
+      for (int p = 0; p < j; ++p) dd -= abs2(S[p][j]);
+      if (!(dd > 0.0) || !isfinite(dd)) {
+        if (!bad) bad = k0 + j + 1;
+        dd = 1.0;
+      }
+      S[j][j] = from_re<T>(sqrt(dd));
+    }
+    __syncthreads();
+    const double rjj = re(S[j][j]);
+    for (int c = j + 1 + tid; c < nb; c += blockDim.x) {
+      T s = S[j][c];
+      for (int p = 0; p < j; ++p) s = sub(s, cmul(S[p][j], S[p][c]));
+      S[j][c] = scal(1.0 / rjj, s);
+    }
+    __syncthreads();
+  }
+  // R^{-1}: column c by back substitution (one thread per column)
+  for (int c = tid; c < nb; c += blockDim.x) {
+    X[c][c] = from_re<T>(1.0 / re(S[c][c]));
+    for (int i = c - 1; i >= 0; --i) {
+      T s = zero<T>();
+      for (int p = i + 1; p <= c; ++p) s = fmac(S[i][p], X[p][c], s);
+      X[i][c] = scal(-1.0 / re(S[i][i]), s);
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < nb * nb; t += blockDim.x) {
+    const int i = t % nb, j = t / nb;
+    if (i <= j) A[(k0 + i) + (long long)(k0 + j) * lda] = S[i][j];
+    Rinv[i + (long long)j * ldr] = (i <= j) ? X[i][j] : zero<T>();
+  }
+  if (tid == 0 && bad && info[b] == 0) info[b] = bad;
+}
+
+// ---------------------------------------------------------------- Jacobi leaves
+constexpr int LEAF_MAX = 64;
+
+template <class T>
+__global__ void __launch_bounds__(256) jacobi_leaf_kernel(const int* offs, const int* sizes, const T* Bg, int ldb,
+                                                          double* lam, T* Vall, int* sweeps_out) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T(*Bs)[LEAF_MAX + 1] = reinterpret_cast<T(*)[LEAF_MAX + 1]>(dyn_smem);
+  T(*Vs)[LEAF_MAX + 1] = Bs + LEAF_MAX;
+  __shared__ double rc[LEAF_MAX / 2], rs[LEAF_MAX / 2];
+  __shared__ T rph[LEAF_MAX / 2];
+  __shared__ int rp[LEAF_MAX / 2], rq[LEAF_MAX / 2];
+  __shared__ double red[32];
+  __shared__ int done;
+  const int l = blockIdx.x;
+  const int off = offs[l], ns = sizes[l];
+  T* V = Vall + (long long)l * LEAF_MAX * LEAF_MAX;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < ns * ns; t += blockDim.x) {
+    const int i = t % ns, j = t / ns;
+    // Hermitian part of the block
+    const T a = Bg[(off + i) + (long long)(off + j) * ldb];
+    const T c = Bg[(off + j) + (long long)(off + i) * ldb];
+    Bs[i][j] = scal(0.5, add(a, conj_(c)));
+    Vs[i][j] = (i == j) ? from_re<T>(1.0) : zero<T>();
+  }
+  __syncthreads();
+  const int nn = ns + (ns & 1);
+  const int npairs = nn / 2;
+  const double u = 0x1p-53;
+  // ||B||_F for the stopping test
+  double acc = 0.0;
+  for (int t = tid; t < ns * ns; t += blockDim.x) acc += abs2(Bs[t % ns][t / ns]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    red[31] = sqrt(s);
+    done = (ns <= 1);
+  }
+  __syncthreads();
+  const double bnorm = red[31];
+  double prev_off = 1e300;
+  int sweep = 0;
+  for (; sweep < 40 && !done; ++sweep) {
+    for (int rd = 0; rd < nn - 1; ++rd) {
+      // round-robin pairing: slot 0 holds player nn-1, the others rotate
+      if (tid < npairs) {
+        int a, bq;
+        if (tid == 0) { a = nn - 1; bq = rd % (nn - 1); }
+        else { a = (rd + tid) % (nn - 1); bq = (rd - tid + (nn - 1)) % (nn - 1); }
+        const int p = min(a, bq), q = max(a, bq);
+        rp[tid] = p; rq[tid] = q;
+        double cc = 1.0, ss = 0.0;
+        T ph = from_re<T>(1.0);
+        if (q < ns) {
+          const T bpq = Bs[p][q];
+          const double apq = sqrt(abs2(bpq));
+          if (apq > 0.0) {
+            const double bpp = re(Bs[p][p]), bqq = re(Bs[q][q]);
+            const double th = (bqq - bpp) / (2.0 * apq);
+            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+            cc = 1.0 / sqrt(1.0 + t * t);
+            ss = t * cc;
+            ph = scal(1.0 / apq, bpq);
+          }
+        }
+        rc[tid] = cc; rs[tid] = ss; rph[tid] = ph;
+      }
+      __syncthreads();
+      // columns of B and V: [x_p, x_q] <- [x_p, x_q] J, J = [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
+      for (int t = tid; t < npairs * ns; t += blockDim.x) {
+        const int pr = t / ns, i = t % ns;
+        const double s = rs[pr];
+        if (s == 0.0) continue;
+        const int p = rp[pr], q = rq[pr];
+        const double c = rc[pr], tau = s / (1.0 + c);
+        const T e = conj_(rph[pr]);
+        {
+          const T x = Bs[i][p], y = mul(e, Bs[i][q]);
+          Bs[i][p] = sub(x, scal(s, add(y, scal(tau, x))));
+          Bs[i][q] = add(y, scal(s, sub(x, scal(tau, y))));
+        }
+        {
+          const T x = Vs[i][p], y = mul(e, Vs[i][q]);
+          Vs[i][p] = sub(x, scal(s, add(y, scal(tau, x))));
+          Vs[i][q] = add(y, scal(s, sub(x, scal(tau, y))));
+        }
+      }
+      __syncthreads();
+      // rows of B: [r_p; r_q] <- J^* [r_p; r_q]
+      for (int t = tid; t < npairs * ns; t += blockDim.x) {
+        const int pr = t / ns, j = t % ns;
+        const double s = rs[pr];
+        if (s == 0.0) continue;
+        const int p = rp[pr], q = rq[pr];
+        const double c = rc[pr], tau = s / (1.0 + c);
+        const T e = rph[pr];
+        const T x = Bs[p][j], y = mul(e, Bs[q][j]);
+        Bs[p][j] = sub(x, scal(s, add(y, scal(tau, x))));
+        Bs[q][j] = add(y, scal(s, sub(x, scal(tau, y))));
+      }
+      __syncthreads();
+      if (tid < npairs && rs[tid] != 0.0) {
+        const int p = rp[tid], q = rq[tid];
+        Bs[p][q] = zero<T>();
+        Bs[q][p] = zero<T>();
+        Bs[p][p] = from_re<T>(re(Bs[p][p]));
+        Bs[q][q] = from_re<T>(re(Bs[q][q]));
+      }
+      __syncthreads();
+    }
+    // off(B) after the sweep
+    double o2 = 0.0;
+    for (int t = tid; t < ns * ns; t += blockDim.x) {
+      const int i = t % ns, j = t / ns;
+      if (i != j) o2 += abs2(Bs[i][j]);
+    }
+    for (int o = 16; o > 0; o >>= 1) o2 += __shfl_down_sync(0xffffffffu, o2, o);
+    if ((tid & 31) == 0) red[tid >> 5] = o2;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+      const double off = sqrt(s);
+      done = (off <= u * bnorm) || (off <= ns * u * bnorm && off >= 0.5 * prev_off) || off == 0.0;
+      red[30] = off;
+    }
+    __syncthreads();
+    prev_off = red[30];
+  }
+  for (int i = tid; i < ns; i += blockDim.x) lam[off + i] = re(Bs[i][i]);
+  for (int t = tid; t < ns * ns; t += blockDim.x) {
+    const int i = t % ns, j = t / ns;
+    V[i + (long long)j * LEAF_MAX] = Vs[i][j];
+  }
+  if (tid == 0 && sweeps_out) sweeps_out[l] = done ? sweep : -sweep;
+}
+
+}  // namespace
+
+template <class T>
+void qr_panel(cudaStream_t st, int m, int n, int band, T* M, int ldm, long long sM, int k0, int nb, T* Y, int ldy,
+              long long sY, T* Tf, long long sT, int batch) {
+  if (nb > PANEL_MAXNB) throw CudaFail{cudaErrorInvalidValue, __FILE__, __LINE__};
+  ProfToken tok = prof_begin(st);
+  qr_panel_kernel<T><<<batch, PANEL_THREADS, 0, st>>>(m, n, band, M, ldm, sM, k0, nb, Y, ldy, sY, Tf, sT);
+  ZCSD_LAUNCH();
+  if (tok.slot >= 0) {
+    // Householder panel: about 4 h nb^2 real flops (dots + rank-1 updates)
+    const double h = std::min(m, k0 + nb - 1 + band) - k0;
+    prof_end(tok, st, PK_QR_PANEL, 4.0 * h * nb * nb * batch * (sizeof(T) == sizeof(double) ? 1.0 : 4.0));
+  }
+}
+
+template <class T>
+void potrf_inv(cudaStream_t st, int n, T* A, int lda, long long sA, int k0, int nb, T* Rinv, int ldr,
+               long long sR, int* info, int batch) {
+  if (nb > CHOL_MAXNB) throw CudaFail{cudaErrorInvalidValue, __FILE__, __LINE__};
+  const int smem = 2 * CHOL_MAXNB * (CHOL_MAXNB + 1) * (int)sizeof(T);
+  ZCSD_CUDA(cudaFuncSetAttribute(potrf_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  ProfToken tok = prof_begin(st);
+  potrf_inv_kernel<T><<<batch, 256, smem, st>>>(n, A, lda, sA, k0, nb, Rinv, ldr, sR, info);
+  ZCSD_LAUNCH();
+  if (tok.slot >= 0) prof_end(tok, st, PK_POTRF, (2.0 / 3.0) * nb * nb * nb * batch);
+}
+
+template <class T>
+void jacobi_leaves(cudaStream_t st, int nleaves, const int* offs, const int* sizes, const T* B, int ldb,
+                   double* lam, T* Vl, int* sweeps_out) {
+  if (nleaves <= 0) return;
+  const int smem = 2 * LEAF_MAX * (LEAF_MAX + 1) * (int)sizeof(T);
+  ZCSD_CUDA(cudaFuncSetAttribute(jacobi_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  ProfToken tok = prof_begin(st);
+  jacobi_leaf_kernel<T><<<nleaves, 256, smem, st>>>(offs, sizes, B, ldb, lam, Vl, sweeps_out);
+  ZCSD_LAUNCH();
+  if (tok.slot >= 0) prof_end(tok, st, PK_JACOBI, 0.0);
+}
+
+#define ZCSD_INST_F(T)                                                                                        \
+  template void qr_panel<T>(cudaStream_t, int, int, int, T*, int, long long, int, int, T*, int, long long, T*, \
+                            long long, int);                                                                 \
+  template void potrf_inv<T>(cudaStream_t, int, T*, int, long long, int, int, T*, int, long long, int*, int); \
+  template void jacobi_leaves<T>(cudaStream_t, int, const int*, const int*, const T*, int, double*, T*, int*);
+
+ZCSD_INST_F(double)
+ZCSD_INST_F(z64)
+
+}  // namespace zcsd

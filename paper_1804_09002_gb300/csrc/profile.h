@@ -1,0 +1,31 @@
+// Per-context kernel timing used by csd_profile_* (see profile.cu).
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+
+namespace zcsd {
+
+struct Profiler {
+  bool enabled = false;
+  struct Rec {
+    int a, b, kind;
+    double flops;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> recs;
+  int used = 0;
+  double ms[PK_KINDS] = {0, 0, 0, 0};
+  double flops[PK_KINDS] = {0, 0, 0, 0};
+  long long count[PK_KINDS] = {0, 0, 0, 0};
+  int event();
+  void flush();
+  void reset();
+  ~Profiler();
+};
+
+// Profiler of the context whose entry point is running on this thread.
+extern thread_local Profiler* t_prof;
+long long launch_count();
+
+}  // namespace zcsd

@@ -1,0 +1,1025 @@
+// Zolo-pd (Section 5), Zolo-eig (Section 5) and the CS decomposition driver
+// (Algorithms 1-3), plus the C ABI declared in include/zolo_csd.h.
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/zolo_csd.h"
+#include "linalg.h"
+#include "profile.h"
+
+namespace zcsd {
+
+constexpr double U_ROUND = 0x1p-53;
+constexpr double EPS_ZOLO = 1e-15;  // interval [eps, 1] of the modified Zolo-pd (Section 5.1)
+constexpr int R_MAX = 8;            // p <= 8 (Section 5)
+
+// ---------------------------------------------------------------- small kernels
+namespace {
+
+template <class T>
+__global__ void diag_phase_kernel(int n, const T* R, int ldr, T* d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const T r = R[i + (long long)i * ldr];
+    const double a = sqrt(abs2(r));
+    d[i] = (a > 0.0) ? scal(1.0 / a, r) : from_re<T>(1.0);
+  }
+}
+
+// Y[:, j] = X[:, j] * d1[j] * conj(d2[j])
+template <class T>
+__global__ void scale_cols_phase_kernel(int m, int n, const T* X, int ldx, const T* d1, const T* d2, T* Y, int ldy) {
+  const long long total = (long long)m * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % m), j = (int)(t / m);
+    Y[i + (long long)j * ldy] = mul(X[i + (long long)j * ldx], mul(d1[j], conj_(d2[j])));
+  }
+}
+
+// D = conj(d1_i) R1[i,j] - conj(d2_i) R2[i,j] on the upper triangle, 0 below
+template <class T>
+__global__ void rdiff_kernel(int n, const T* R1, int ld1, const T* d1, const T* R2, int ld2, const T* d2, T* D) {
+  const long long total = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    T v = zero<T>();
+    if (i <= j) v = sub(cmul(d1[i], R1[i + (long long)j * ld1]), cmul(d2[i], R2[i + (long long)j * ld2]));
+    D[t] = v;
+  }
+}
+
+// B = H2 - H1 + mu (I - G), G = A1^* A1 + A2^* A2 (G may be null when mu = 0)
+template <class T>
+__global__ void form_b_kernel(int n, const T* H, long long sH, const T* G, double mu, T* B) {
+  const long long total = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    T v = sub(H[sH + t], H[t]);
+    if (mu != 0.0) {
+      T im = scal(-1.0, G[t]);
+      if (i == j) im = add(im, from_re<T>(1.0));
+      v = add(v, scal(mu, im));
+    }
+    B[t] = v;
+  }
+}
+
+__global__ void zero_tail_kernel(int n, int r, double* theta) {
+  for (int i = r + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) theta[i] = 0.0;
+}
+
+int grid_for(long long total) { return (int)std::min<long long>((total + 255) / 256, 152 * 8); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- context
+struct Plan {
+  int steps = 0;
+  int r[4];
+  double ell[4];
+  double c[4][2 * R_MAX], a[4][R_MAX], mhat[4], sqrtc[4][R_MAX], w[4][R_MAX];
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  HostScalars hs;
+  Plan plan;
+  bool plan_ready = false;
+  unsigned long long seed = 0x5EEDull;
+  Profiler prof;
+};
+
+static const Plan& get_plan(Ctx& cx) {
+  if (!cx.plan_ready) {
+    Plan& p = cx.plan;
+    p.steps = zolo_plan(EPS_ZOLO, R_MAX, 4, p.r, p.ell);
+    for (int s = 0; s < p.steps; ++s) {
+      double next;
+      zolo_coeffs(p.ell[s], p.r[s], p.c[s], p.a[s], &p.mhat[s], &next);
+      for (int j = 0; j < p.r[s]; ++j) {
+        p.sqrtc[s][j] = std::sqrt(p.c[s][2 * j]);
+        p.w[s][j] = p.mhat[s] * p.a[s][j] / p.sqrtc[s][j];
+      }
+    }
+    cx.plan_ready = true;
+  }
+  return cx.plan;
+}
+
+static void d2h(Ctx& cx, void* dst, const void* src, size_t bytes) {
+  ZCSD_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, cx.stream));
+  ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+}
+
+// ---------------------------------------------------------------- Zolo-pd
+struct PolarDiag {
+  int chol_fallback = 0;
+};
+
+// W_p = Zolo-pd polar factor of X0_p (p < P), X0 with ||X0_p||_2 <= 1 (ld n,
+// stride n*n).  W may alias nothing else.  Section 5: iterates
+// X_{k+1} = M (X_k + sum_j a_j X_k (X_k^* X_k + c_{2j-1} I)^{-1}); the first
+// iteration in QR form (X (X^*X + cI)^{-1} = Q1 Q2^* / sqrt(c) for
+// [X; sqrt(c) I] = [Q1; Q2] R), later ones in Cholesky form.
+template <class T>
+void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd) {
+  cudaStream_t st = cx.stream;
+  const Plan& pl = get_plan(cx);
+  const long long nn = (long long)n * n;
+  const size_t mk = ar.mark();
+  T* Xa = ar.get<T>(nn * P);
+  T* Xb = ar.get<T>(nn * P);
+  axpby<T>(st, n, n, 1.0, X0, n, nn, 0.0, Xa, n, nn, P);
+  T* X = Xa;
+  T* Xn = Xb;
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
+  for (int s = 0; s < pl.steps; ++s) {
+    const int r = pl.r[s];
+    bool use_qr = (s == 0);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const size_t mk2 = ar.mark();
+      if (use_qr) {
+        // ---- QR form on the stacked [X; sqrt(c_{2j-1}) I], 2n x n, P*r problems
+        const int m2 = 2 * n;
+        const long long sM = (long long)m2 * n;
+        T* M = ar.get<T>(sM * P * r);
+        T* E = ar.get<T>(sM * P * r);
+        stack_terms<T>(st, n, X, n, nn, pl.sqrtc[s], r, M, m2, sM, P);
+        QRStore<T> q = qr_alloc<T>(ar, m2, n, n + 1, P * r);
+        qr_factor<T>(st, ar, q, M, m2, sM);
+        qr_form_q<T>(st, ar, q, E, m2, sM);
+        // X_new = mhat X + sum_j (mhat a_j / sqrt(c_j)) Q1_j Q2_j^*   (Q2 upper triangular)
+        GemmArgs<T> g;
+        g.batch = P;
+        g.m = n; g.n = n; g.k = n; g.opA = OP_N; g.opB = OP_C;
+        g.A = E; g.lda = m2; g.sA = sM * r; g.sAj = sM;
+        g.B = E + n; g.ldb = m2; g.sB = sM * r; g.sBj = sM;
+        g.nsum = r;
+        for (int j = 0; j < r; ++j) g.w[j] = pl.w[s][j];
+        g.Cin = X; g.ldcin = n; g.sCin = nn;
+        g.C = Xn; g.ldc = n; g.sC = nn;
+        g.alpha = one; g.beta = from_re<T>(pl.mhat[s]);
+        g.kflags = K_FROM_COL;
+        gemm(g, st);
+        ar.release(mk2);
+        break;
+      }
+      // ---- Cholesky form: Z_j = X^* X + c_{2j-1} I = R^* R, T_j = X R^{-1} R^{-*}
+      T* G = ar.get<T>(nn * P);
+      T* Z = ar.get<T>(nn * P * r);
+      T* Rinv = ar.get<T>((size_t)NB_CHOL * n * P * r);
+      T* Yt = ar.get<T>(nn * P * r);
+      T* Tt = ar.get<T>(nn * P * r);
+      int* info = ar.get<int>(P * r);
+      GemmArgs<T> g;
+      g.batch = P;
+      g.m = n; g.n = n; g.k = n; g.opA = OP_C; g.opB = OP_N;
+      g.A = X; g.lda = n; g.sA = nn;
+      g.B = X; g.ldb = n; g.sB = nn;
+      g.C = G; g.ldc = n; g.sC = nn;
+      g.alpha = one; g.beta = zer; g.uplo = 1;
+      gemm(g, st);
+      double shifts[R_MAX];
+      for (int j = 0; j < r; ++j) shifts[j] = pl.c[s][2 * j];
+      shift_terms<T>(st, n, G, n, nn, shifts, r, Z, n, nn, P);
+      cholesky<T>(st, n, Z, n, nn, Rinv, (long long)NB_CHOL * n, info, P * r);
+      d2h(cx, cx.hs.i, info, sizeof(int) * P * r);
+      bool ok = true;
+      for (int q = 0; q < P * r; ++q) ok = ok && (cx.hs.i[q] == 0);
+      if (!ok) {
+        // non-positive pivot: redo this iteration in QR form
+        ar.release(mk2);
+        use_qr = true;
+        if (pd) pd->chol_fallback += 1;
+        continue;
+      }
+      trsm_pair<T>(st, ar, n, X, n, nn, r, Z, n, nn, Rinv, (long long)NB_CHOL * n, Yt, Tt, n, nn, P * r);
+      double aa[R_MAX];
+      for (int j = 0; j < r; ++j) aa[j] = pl.a[s][j];
+      sum_terms<T>(st, n, pl.mhat[s], X, n, nn, aa, r, Tt, n, nn, Xn, n, nn, P);
+      ar.release(mk2);
+      break;
+    }
+    std::swap(X, Xn);
+    (void)mone;
+  }
+  axpby<T>(st, n, n, 1.0, X, n, nn, 0.0, W, n, nn, P);
+  ar.release(mk);
+}
+
+// ---------------------------------------------------------------- Zolo-eig
+struct EigDiag {
+  int splits = 0, retries = 0, leaves = 0;
+  double offblock = 0.0;
+  int status = 0;
+};
+
+// Eigendecomposition of the Hermitian n x n matrix Bin (device, ld ldb) by
+// spectral divide and conquer (Section 5).  Writes lam (device, length n) and
+// V (device, ld n).  If split_at is finite, only eigenpairs below it are
+// computed (Section 5.2: split at 1.1 for Algorithm 3); they occupy columns
+// [*lo, n) on return.  Eigenvalues in [*lo, n) are sorted ascending with V.
+template <class T>
+void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T* V, double split_at, int* lo_out,
+               EigDiag* ed) {
+  cudaStream_t st = cx.stream;
+  const long long nn = (long long)n * n;
+  const size_t mk = ar.mark();
+  T* Bw = ar.get<T>(nn);
+  T* Xs = ar.get<T>(nn);
+  T* Ws = ar.get<T>(nn);
+  T* Ps = ar.get<T>(nn);
+  T* Om = ar.get<T>(nn);
+  T* Qf = ar.get<T>(nn);
+  T* Tmp = ar.get<T>(nn);
+  double* dsc = ar.get<double>(n + 64);  // diag copy + scalars
+  double* scratch = ar.get<double>(304 * 4);
+  double* lamw = ar.get<double>(n);
+  int* perm = ar.get<int>(n);
+  symmetrize<T>(st, n, Bin, ldb, 0, Bw, n, 0, 1);
+  set_eye<T>(st, n, n, V, n, 0, 1);
+  double* dvals = dsc;       // n
+  double* sc = dsc + n;      // scalars
+  fro2<T>(st, n, n, Bw, n, 0, 0.0, sc, 1, scratch);
+  d2h(cx, cx.hs.d, sc, sizeof(double));
+  const double bnorm = std::sqrt(cx.hs.d[0]);
+  static const bool debug = getenv("ZCSD_DEBUG") != nullptr;
+
+  struct Blk { int off, sz; bool top; };
+  std::vector<Blk> stack;
+  stack.push_back({0, n, true});
+  std::vector<int> leaf_off, leaf_sz;
+  int lo = 0;
+  const bool restricted = std::isfinite(split_at);
+  const T one = from_re<T>(1.0), zer = zero<T>();
+  while (!stack.empty()) {
+    Blk bk = stack.back();
+    stack.pop_back();
+    const int off = bk.off, sz = bk.sz;
+    if (sz <= 0) continue;
+    T* Bsub = Bw + off + (long long)off * n;
+    if (sz <= LEAF && !(bk.top && restricted)) {
+      leaf_off.push_back(off);
+      leaf_sz.push_back(sz);
+      continue;
+    }
+    // block norm for the scalar-block test
+    fro2<T>(st, sz, sz, Bsub, n, 0, 0.0, sc, 1, scratch);
+    diag_real<T>(st, sz, Bsub, n, dvals);
+    median(st, sz, dvals, sc + 1);
+    d2h(cx, cx.hs.d, sc, 2 * sizeof(double));
+    const double bsub_norm = std::sqrt(cx.hs.d[0]);
+    double s = (bk.top && restricted) ? split_at : cx.hs.d[1];
+    bool done = false;
+    // Accepted rounding levels: a block within scal_tol of s I is scalar; a
+    // split is accepted when ||B'_21||_F <= off_tol.  Both are measured
+    // against ||B||_F of the whole matrix, which is what the backward error
+    // of the eigendecomposition is relative to.
+    const double scal_tol = 100.0 * U_ROUND * bnorm * std::sqrt((double)sz);
+    const double off_tol = 20.0 * U_ROUND * bnorm * std::sqrt((double)sz);
+    const double s0 = s;
+    for (int attempt = 0; attempt < 7 && !done; ++attempt) {
+      if (attempt > 0) {
+        ed->retries += 1;
+        // shifts s0 + (+1, -1, +2, -2, +4, -4) * 1e-3 ||B_sub||_F / sqrt(sz)
+        const double mag = (double)(1 << ((attempt - 1) / 2)) * (attempt & 1 ? 1.0 : -1.0);
+        s = s0 + 1e-3 * mag * bsub_norm / std::sqrt((double)sz);
+      }
+      // X = (B - sI) / ||B - sI||_F
+      fro2<T>(st, sz, sz, Bsub, n, 0, s, sc + 2, 1, scratch);
+      d2h(cx, cx.hs.d, sc + 2, sizeof(double));
+      const double xnorm = std::sqrt(cx.hs.d[0]);
+      if (xnorm <= scal_tol) {
+        // B_sub = sI to working precision: every vector is an eigenvector
+        if (bk.top && restricted) lo = (s < split_at) ? off : off + sz;
+        else { leaf_off.push_back(off); leaf_sz.push_back(-sz); }
+        done = true;
+        break;
+      }
+      // device copies of s and ||B - sI||_F for the scaling kernel (the next
+      // device-to-host read synchronises the stream before hs is reused)
+      cx.hs.d[10] = s;
+      cx.hs.d[11] = xnorm;
+      ZCSD_CUDA(cudaMemcpyAsync(sc + 3, &cx.hs.d[10], 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+      shift_scale<T>(st, sz, Bsub, n, sc + 3, sc + 4, Xs, sz);
+      zolo_pd<T>(cx, ar, sz, 1, Xs, Ws, nullptr);
+      // P = (W + I)/2, k = trace(P) = number of eigenvalues above s
+      half_plus_eye<T>(st, sz, Ws, sz, Ps, sz);
+      diag_real<T>(st, sz, Ps, sz, dvals);
+      sum_vec(st, sz, dvals, sc + 5);
+      d2h(cx, cx.hs.d, sc + 5, sizeof(double));
+      const double tr = cx.hs.d[0];
+      const int k = (int)std::floor(tr + 0.5);
+      if (debug)
+        fprintf(stderr, "zolo-eig: off=%d sz=%d attempt=%d s=%.17g |B-sI|=%.3e trace=%.6f\n", off, sz, attempt, s,
+                xnorm, tr);
+      if (!(std::fabs(tr - k) <= 0.25) || ((k == 0 || k == sz) && !(bk.top && restricted))) continue;
+      if (bk.top && restricted && (k == 0 || k == sz)) {
+        lo = (k == sz) ? off + sz : off;  // all above / all below the split point
+        if (k == 0) { stack.push_back({off, sz, false}); }
+        done = true;
+        break;
+      }
+      // subspaces: [Q1 Q2] = qr(P Omega), Q1 spans range(P)
+      randn<T>(st, sz, sz, Om, sz, cx.seed + 7919ull * (unsigned long long)(ed->splits * 4 + attempt));
+      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Ps, sz, Om, sz, zer, Tmp, sz);
+      {
+        const size_t mq = ar.mark();
+        QRStore<T> q = qr_alloc<T>(ar, sz, sz, sz, 1);
+        qr_factor<T>(st, ar, q, Tmp, sz, 0);
+        qr_form_q<T>(st, ar, q, Qf, sz, 0);
+        ar.release(mq);
+      }
+      // B' = Q^* B_sub Q
+      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Bsub, n, Qf, sz, zer, Tmp, sz);
+      gemm1<T>(st, OP_C, OP_N, sz, sz, sz, one, Qf, sz, Tmp, sz, zer, Xs, sz);
+      fro2<T>(st, sz - k, k, Xs + k, sz, 0, 0.0, sc + 6, 1, scratch);
+      d2h(cx, cx.hs.d, sc + 6, sizeof(double));
+      const double offa = std::sqrt(cx.hs.d[0]);
+      if (debug) fprintf(stderr, "zolo-eig:   k=%d ||B21||=%.3e tol=%.3e\n", k, offa, off_tol);
+      if (!(offa <= off_tol)) continue;
+      ed->offblock = std::max(ed->offblock, offa / std::max(bnorm, 1e-300));
+      ed->splits += 1;
+      // accept: B_sub <- B', V[:, off:off+sz] <- V[:, off:off+sz] Q
+      axpby<T>(st, sz, sz, 1.0, Xs, sz, 0, 0.0, Bsub, n, 0, 1);
+      gemm1<T>(st, OP_N, OP_N, n, sz, sz, one, V + (long long)off * n, n, Qf, sz, zer, Tmp, n);
+      axpby<T>(st, n, sz, 1.0, Tmp, n, 0, 0.0, V + (long long)off * n, n, 0, 1);
+      if (bk.top && restricted) {
+        lo = off + k;
+        stack.push_back({off + k, sz - k, false});
+      } else {
+        stack.push_back({off + k, sz - k, false});
+        stack.push_back({off, k, false});
+      }
+      done = true;
+    }
+    if (!done) {
+      ed->status = CSD_ERR_EIG_SPLIT;
+      throw ed;
+    }
+  }
+  // ---- leaves: Jacobi on blocks <= LEAF; scalar blocks keep their diagonal
+  std::vector<int> jo, js;
+  for (size_t i = 0; i < leaf_off.size(); ++i) {
+    if (leaf_sz[i] > 0) { jo.push_back(leaf_off[i]); js.push_back(leaf_sz[i]); }
+    else diag_real<T>(st, -leaf_sz[i], Bw + leaf_off[i] + (long long)leaf_off[i] * n, n, lamw + leaf_off[i]);
+  }
+  const int nl = (int)jo.size();
+  ed->leaves = nl;
+  if (nl > 0) {
+    const size_t ml = ar.mark();
+    int* doffs = ar.get<int>(2 * nl);
+    T* Vl = ar.get<T>((size_t)LEAF * LEAF * nl);
+    std::vector<int> hbuf(2 * nl);
+    for (int i = 0; i < nl; ++i) { hbuf[i] = jo[i]; hbuf[nl + i] = js[i]; }
+    ZCSD_CUDA(cudaMemcpyAsync(doffs, hbuf.data(), sizeof(int) * 2 * nl, cudaMemcpyHostToDevice, st));
+    jacobi_leaves<T>(st, nl, doffs, doffs + nl, Bw, n, lamw, Vl, nullptr);
+    for (int i = 0; i < nl; ++i) {
+      gemm1<T>(st, OP_N, OP_N, n, js[i], js[i], one, V + (long long)jo[i] * n, n,
+               Vl + (long long)i * LEAF * LEAF, LEAF, zer, Tmp, n);
+      axpby<T>(st, n, js[i], 1.0, Tmp, n, 0, 0.0, V + (long long)jo[i] * n, n, 0, 1);
+    }
+    ZCSD_CUDA(cudaStreamSynchronize(st));  // hbuf lifetime
+    ar.release(ml);
+  }
+  // ---- sort the computed eigenpairs [lo, n) ascending
+  const int cnt = n - lo;
+  if (cnt > 0) {
+    sort_perm(st, cnt, lamw + lo, perm);
+    gather_vec(st, cnt, lamw + lo, perm, lam + lo);
+    gather_cols<T>(st, n, cnt, V + (long long)lo * n, n, perm, Tmp, n);
+    axpby<T>(st, n, cnt, 1.0, Tmp, n, 0, 0.0, V + (long long)lo * n, n, 0, 1);
+  }
+  if (lo > 0) ZCSD_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * lo, st));
+  *lo_out = lo;
+  ar.release(mk);
+}
+
+// ---------------------------------------------------------------- CSD
+template <class T>
+int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int lda2, T* U1, int ldu1, T* U2,
+             int ldu2, T* V1, int ldv1, double* theta, int* rank_out, csd_info* info) {
+  cudaStream_t st = cx.stream;
+  const long long nn = (long long)n * n;
+  const Plan& pl = get_plan(cx);
+  T* Apk = ar.get<T>(2 * nn);   // [A1 | A2] packed, ld n
+  T* W = ar.get<T>(2 * nn);
+  T* H = ar.get<T>(2 * nn);
+  T* Bm = ar.get<T>(nn);
+  T* V = ar.get<T>(nn);
+  T* Ut = ar.get<T>(2 * nn);
+  double* lam = ar.get<double>(n);
+  double* dv = ar.get<double>(4 * n + 64);
+  double* scratch = ar.get<double>(304 * 4);
+  int* perm = ar.get<int>(n);
+  double* sc = dv + 4 * n;
+  axpby<T>(st, n, n, 1.0, A1, lda1, 0, 0.0, Apk, n, 0, 1);
+  axpby<T>(st, n, n, 1.0, A2, lda2, 0, 0.0, Apk + nn, n, 0, 1);
+  // ---- input checks and rank (remark (vi): ||A||_F^2 ~ rank)
+  count_nonfinite<T>(st, n, 2 * n, Apk, n, sc, scratch);
+  fro2<T>(st, n, n, Apk, n, nn, 0.0, sc + 1, 2, scratch);
+  d2h(cx, cx.hs.d, sc, 3 * sizeof(double));
+  if (cx.hs.d[0] != 0.0) return CSD_ERR_NONFINITE;
+  const double fro = cx.hs.d[1] + cx.hs.d[2];
+  int r = (int)std::floor(fro + 0.5);
+  r = std::max(0, std::min(n, r));
+  const double mu = (r == n) ? 0.0 : 2.0;
+  if (info) {
+    info->rank = r;
+    info->mu = mu;
+    info->zolo_iters = pl.steps;
+    for (int s = 0; s < 4; ++s) {
+      info->r_terms[s] = s < pl.steps ? pl.r[s] : 0;
+      info->ell[s] = s < pl.steps ? pl.ell[s] : 0.0;
+    }
+  }
+  // ---- lines 1-2: W_i H_i = A_i (both polar decompositions in one batch)
+  PolarDiag pd;
+  zolo_pd<T>(cx, ar, n, 2, Apk, W, &pd);
+  const T one = from_re<T>(1.0), zer = zero<T>();
+  {
+    GemmArgs<T> g;  // H_i = sym(W_i^* A_i)
+    g.batch = 2;
+    g.m = n; g.n = n; g.k = n; g.opA = OP_C; g.opB = OP_N;
+    g.A = W; g.lda = n; g.sA = nn;
+    g.B = Apk; g.ldb = n; g.sB = nn;
+    g.C = H; g.ldc = n; g.sC = nn;
+    g.alpha = one; g.beta = zer;
+    gemm(g, st);
+    symmetrize<T>(st, n, H, n, nn, H, n, nn, 2);
+  }
+  // ---- orthogonality of W_i; Algorithm 2 where W_i is not orthonormal
+  {
+    const size_t mk = ar.mark();
+    T* Gw = ar.get<T>(2 * nn);
+    GemmArgs<T> g;
+    g.batch = 2;
+    g.m = n; g.n = n; g.k = n; g.opA = OP_C; g.opB = OP_N;
+    g.A = W; g.lda = n; g.sA = nn;
+    g.B = W; g.ldb = n; g.sB = nn;
+    g.C = Gw; g.ldc = n; g.sC = nn;
+    g.alpha = one; g.beta = zer;
+    gemm(g, st);
+    fro2<T>(st, n, n, Gw, n, nn, 1.0, sc + 4, 2, scratch);
+    d2h(cx, cx.hs.d, sc + 4, 2 * sizeof(double));
+    ar.release(mk);
+  }
+  const double orth[2] = {std::sqrt(cx.hs.d[0]), std::sqrt(cx.hs.d[1])};
+  int status = CSD_OK;
+  if (info) {
+    info->orth_err[0] = orth[0];
+    info->orth_err[1] = orth[1];
+    info->chol_fallback = pd.chol_fallback;
+  }
+  const double orth_tol = 50.0 * n * U_ROUND;
+  for (int i = 0; i < 2 && mu == 0.0; ++i) {
+    if (orth[i] <= orth_tol) continue;
+    // Algorithm 2: A_i = Q_i R_i, H_i = Q~ R~, W_i = Q_i Q~^* (diag(R) >= 0)
+    const size_t mk = ar.mark();
+    T* Ma = ar.get<T>(nn);
+    T* Mh = ar.get<T>(nn);
+    T* Qa = ar.get<T>(nn);
+    T* Qh = ar.get<T>(nn);
+    T* d1 = ar.get<T>(n);
+    T* d2 = ar.get<T>(n);
+    T* D = ar.get<T>(nn);
+    axpby<T>(st, n, n, 1.0, Apk + i * nn, n, 0, 0.0, Ma, n, 0, 1);
+    axpby<T>(st, n, n, 1.0, H + i * nn, n, 0, 0.0, Mh, n, 0, 1);
+    {
+      const size_t mq = ar.mark();
+      QRStore<T> qa = qr_alloc<T>(ar, n, n, n, 1);
+      qr_factor<T>(st, ar, qa, Ma, n, 0);
+      qr_form_q<T>(st, ar, qa, Qa, n, 0);
+      ar.release(mq);
+      QRStore<T> qh = qr_alloc<T>(ar, n, n, n, 1);
+      qr_factor<T>(st, ar, qh, Mh, n, 0);
+      qr_form_q<T>(st, ar, qh, Qh, n, 0);
+      ar.release(mq);
+    }
+    diag_phase_kernel<T><<<ceil_div(n, 256), 256, 0, st>>>(n, Ma, n, d1);
+    diag_phase_kernel<T><<<ceil_div(n, 256), 256, 0, st>>>(n, Mh, n, d2);
+    ZCSD_LAUNCH();
+    scale_cols_phase_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, n, Qa, n, d1, d2, Qa, n);
+    ZCSD_LAUNCH();
+    gemm1<T>(st, OP_N, OP_C, n, n, n, one, Qa, n, Qh, n, zer, W + i * nn, n);
+    rdiff_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, Ma, n, d1, Mh, n, d2, D);
+    ZCSD_LAUNCH();
+    fro2<T>(st, n, n, D, n, 0, 0.0, sc + 8, 1, scratch);
+    rdiff_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, Ma, n, d1, Ma, n, d1, D);  // zero; reuse for ||R||
+    ZCSD_LAUNCH();
+    fro2<T>(st, n, n, Ma, n, 0, 0.0, sc + 9, 1, scratch);  // ||R|| + ||V below||: upper bound
+    d2h(cx, cx.hs.d, sc + 8, 2 * sizeof(double));
+    const double rd = std::sqrt(cx.hs.d[0]) / std::max(std::sqrt(fro / 2.0), 1e-300);
+    if (info) { info->alg2_used[i] = 1; info->rdiff[i] = rd; }
+    if (rd > 1e3 * n * U_ROUND) status = CSD_WARN_ALG2_RCHECK;
+    ar.release(mk);
+  }
+  // ---- line 4: B = H2 - H1 + mu (I - A^* A)
+  {
+    const size_t mk = ar.mark();
+    T* G = nullptr;
+    if (mu != 0.0) {
+      G = ar.get<T>(nn);
+      GemmArgs<T> g;  // A^* A = A1^* A1 + A2^* A2 (two-term grouped sum)
+      g.batch = 1;
+      g.m = n; g.n = n; g.k = n; g.opA = OP_C; g.opB = OP_N;
+      g.A = Apk; g.lda = n; g.sAj = nn;
+      g.B = Apk; g.ldb = n; g.sBj = nn;
+      g.nsum = 2;
+      g.C = G; g.ldc = n;
+      g.alpha = one; g.beta = zer;
+      gemm(g, st);
+    }
+    form_b_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, H, nn, G, mu, Bm);
+    ZCSD_LAUNCH();
+    symmetrize<T>(st, n, Bm, n, 0, Bm, n, 0, 1);
+    ar.release(mk);
+  }
+  // ---- line 5: V1 Lambda V1^* = B (Zolo-eig; Algorithm 3 keeps Lambda < 1.1)
+  EigDiag ed;
+  int lo = 0;
+  heig_impl<T>(cx, ar, n, Bm, n, lam, V, mu != 0.0 ? 1.1 : INFINITY, &lo, &ed);
+  const int rk = n - lo;
+  if (info) {
+    info->eig_splits = ed.splits;
+    info->eig_retries = ed.retries;
+    info->eig_leaves = ed.leaves;
+    info->eig_offblock = ed.offblock;
+  }
+  // ---- lines 6-9: U_i = W_i V1, C/S = diag(V1^* H_i V1), theta = atan2(S, C)
+  T* Vr = V + (long long)lo * n;
+  if (rk > 0) {
+    GemmArgs<T> g;
+    g.batch = 2;
+    g.m = n; g.n = rk; g.k = n; g.opA = OP_N; g.opB = OP_N;
+    g.A = W; g.lda = n; g.sA = nn;
+    g.B = Vr; g.ldb = n; g.sB = 0;
+    g.C = Ut; g.ldc = n; g.sC = nn;
+    g.alpha = one; g.beta = zer;
+    gemm(g, st);
+    T* HV = W;  // W no longer needed
+    GemmArgs<T> g2 = g;
+    g2.A = H;
+    g2.C = HV;
+    gemm(g2, st);
+    double* Cd = dv;
+    double* Sd = dv + n;
+    double* th = dv + 2 * n;
+    col_dots<T>(st, n, rk, Vr, n, HV, n, Cd);
+    col_dots<T>(st, n, rk, Vr, n, HV + nn, n, Sd);
+    theta_from_cs(st, rk, Cd, Sd, th);
+    sort_perm(st, rk, th, perm);
+    gather_vec(st, rk, th, perm, theta);
+    gather_cols<T>(st, n, rk, Ut, n, perm, U1, ldu1);
+    gather_cols<T>(st, n, rk, Ut + nn, n, perm, U2, ldu2);
+    gather_cols<T>(st, n, rk, Vr, n, perm, V1, ldv1);
+  }
+  if (rk < n) {
+    zero_tail_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, rk, theta);
+    ZCSD_LAUNCH();
+  }
+  ZCSD_CUDA(cudaStreamSynchronize(st));
+  if (rank_out) *rank_out = rk;
+  if (info) info->rank = rk;
+  return status;
+}
+
+template <class T>
+int polar_impl(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* Wo, int ldw, T* Ho, int ldh, csd_info* info) {
+  cudaStream_t st = cx.stream;
+  const long long nn = (long long)n * n;
+  T* X = ar.get<T>(nn);
+  T* W = ar.get<T>(nn);
+  double* sc = ar.get<double>(64);
+  double* scratch = ar.get<double>(304 * 4);
+  axpby<T>(st, n, n, 1.0, A, lda, 0, 0.0, X, n, 0, 1);
+  count_nonfinite<T>(st, n, n, X, n, sc, scratch);
+  fro2<T>(st, n, n, X, n, 0, 0.0, sc + 1, 1, scratch);
+  d2h(cx, cx.hs.d, sc, 2 * sizeof(double));
+  if (cx.hs.d[0] != 0.0) return CSD_ERR_NONFINITE;
+  const double fn = std::sqrt(cx.hs.d[1]);
+  // ||A||_2 <= 1 is needed; rescale by ||A||_F only when it could be violated
+  const double alpha = (fn > 1.0) ? 1.0 / fn : 1.0;
+  if (alpha != 1.0) axpby<T>(st, n, n, alpha, X, n, 0, 0.0, X, n, 0, 1);
+  PolarDiag pd;
+  zolo_pd<T>(cx, ar, n, 1, X, W, &pd);
+  axpby<T>(st, n, n, 1.0, W, n, 0, 0.0, Wo, ldw, 0, 1);
+  if (Ho) {
+    T* Hm = X;
+    gemm1<T>(st, OP_C, OP_N, n, n, n, from_re<T>(1.0), W, n, A, lda, zero<T>(), Hm, n);
+    symmetrize<T>(st, n, Hm, n, 0, Ho, ldh, 0, 1);
+  }
+  if (info) {
+    const Plan& pl = get_plan(cx);
+    info->zolo_iters = pl.steps;
+    for (int s = 0; s < 4; ++s) {
+      info->r_terms[s] = s < pl.steps ? pl.r[s] : 0;
+      info->ell[s] = s < pl.steps ? pl.ell[s] : 0.0;
+    }
+    info->chol_fallback = pd.chol_fallback;
+  }
+  ZCSD_CUDA(cudaStreamSynchronize(st));
+  return CSD_OK;
+}
+
+template <class T>
+int heig_entry(Ctx& cx, Arena& ar, int n, const T* B, int ldb, double* lam, T* Vo, int ldv, csd_info* info) {
+  cudaStream_t st = cx.stream;
+  const long long nn = (long long)n * n;
+  T* V = ar.get<T>(nn);
+  double* sc = ar.get<double>(64);
+  double* scratch = ar.get<double>(304 * 4);
+  count_nonfinite<T>(st, n, n, B, ldb, sc, scratch);
+  d2h(cx, cx.hs.d, sc, sizeof(double));
+  if (cx.hs.d[0] != 0.0) return CSD_ERR_NONFINITE;
+  EigDiag ed;
+  int lo = 0;
+  heig_impl<T>(cx, ar, n, B, ldb, lam, V, INFINITY, &lo, &ed);
+  axpby<T>(st, n, n, 1.0, V, n, 0, 0.0, Vo, ldv, 0, 1);
+  if (info) {
+    info->eig_splits = ed.splits;
+    info->eig_retries = ed.retries;
+    info->eig_leaves = ed.leaves;
+    info->eig_offblock = ed.offblock;
+  }
+  ZCSD_CUDA(cudaStreamSynchronize(st));
+  return CSD_OK;
+}
+
+}  // namespace zcsd
+
+// ====================================================================== C ABI
+using namespace zcsd;
+
+struct csd_ctx {
+  Ctx cx;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Upper bound of the workspace (bytes) needed by a call; the driver also
+// grows the arena and retries if a bound turns out short.
+size_t polar_bytes(long long n, int P, size_t es) {
+  const long long nn = n * n;
+  const long long r = R_MAX;
+  long long qr = 2 * (2 * nn) * P * r                                         // M, E
+                 + (long long)ceil_div(n, NB_QR) * (n + 1 + NB_QR) * NB_QR * P * r  // Y
+                 + (long long)ceil_div(n, NB_QR) * NB_QR * NB_QR * P * r           // T
+                 + 2LL * NB_QR * n * P * r;                                         // W, W2
+  long long ch = nn * P + 3 * nn * P * r + (long long)NB_CHOL * n * P * r * 2;
+  return (size_t)((2 * nn * P + std::max(qr, ch)) * es) + 64 * 256;
+}
+
+size_t heig_bytes(long long n, size_t es) {
+  const long long nn = n * n;
+  long long qr = (long long)ceil_div(n, NB_QR) * (n + NB_QR) * NB_QR + (long long)ceil_div(n, NB_QR) * NB_QR * NB_QR +
+                 2LL * NB_QR * n;
+  long long leaves = (n / 1 + 1) * 0 + (long long)LEAF * LEAF * (n / 1);
+  return (size_t)((7 * nn + std::max(qr, leaves)) * es) + polar_bytes(n, 1, es) + (size_t)(3 * n + 2048) * 8 + 64 * 256;
+}
+
+size_t csd_bytes(long long n, size_t es) {
+  const long long nn = n * n;
+  size_t fixed = (size_t)(11 * nn * es) + (size_t)(6 * n + 2048) * 8 + 64 * 256;
+  size_t alg2 = (size_t)(7 * nn * es) + polar_bytes(1, 1, es);
+  return fixed + std::max({polar_bytes(n, 2, es), heig_bytes(n, es), alg2 + (size_t)(2 * nn * es)});
+}
+
+int ensure_ws(Ctx& cx, size_t bytes) {
+  if (cx.ws_bytes >= bytes) return 0;
+  if (cx.ws) {
+    cudaStreamSynchronize(cx.stream);
+    cudaFree(cx.ws);
+    cx.ws = nullptr;
+    cx.ws_bytes = 0;
+  }
+  if (cudaMalloc((void**)&cx.ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cx.ws = nullptr;
+    return CSD_ERR_ALLOC;
+  }
+  cx.ws_bytes = bytes;
+  return 0;
+}
+
+// Run `body(arena)` with a workspace of at least `need` bytes, growing it on
+// an arena overflow; translates exceptions to status codes.
+template <class F>
+int run_with_ws(Ctx& cx, size_t need, csd_info* info, F body) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int status = CSD_OK;
+  if (cudaSetDevice(cx.device) != cudaSuccess) { cudaGetLastError(); return CSD_ERR_CUDA; }
+  struct ProfScope {  // make this context's profiler the thread's active one
+    Profiler* prev;
+    explicit ProfScope(Profiler* p) : prev(t_prof) { t_prof = p; }
+    ~ProfScope() { t_prof = prev; }
+  } scope(&cx.prof);
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    status = ensure_ws(cx, need);
+    if (status) break;
+    Arena ar;
+    ar.base = cx.ws;
+    ar.cap = cx.ws_bytes;
+    try {
+      status = body(ar);
+      break;
+    } catch (ArenaOverflow& o) {
+      cudaStreamSynchronize(cx.stream);
+      need = std::max(need * 2, o.needed + need / 2);
+      status = CSD_ERR_INTERNAL;
+    } catch (CudaFail& f) {
+      fprintf(stderr, "zolo_csd: CUDA error %s at %s:%d\n", cudaGetErrorString(f.err), f.file, f.line);
+      status = CSD_ERR_CUDA;
+      break;
+    } catch (EigDiag*) {
+      status = CSD_ERR_EIG_SPLIT;
+      break;
+    } catch (std::bad_alloc&) {
+      status = CSD_ERR_ALLOC;
+      break;
+    }
+  }
+  const auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    info->status = status;
+    info->ms_total = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  }
+  return status;
+}
+
+// Device view of a caller matrix: the pointer itself when it is device
+// memory, else a staging copy in the arena (copied in when `in`).
+template <class T>
+struct Mat {
+  T* d = nullptr;
+  int ld = 0;
+  const void* host = nullptr;
+  void* host_out = nullptr;
+  int host_ld = 0;
+};
+
+template <class T>
+Mat<T> view_in(Ctx& cx, Arena& ar, const void* p, int ld, int m, int n) {
+  Mat<T> v;
+  if (is_device_ptr(p)) {
+    v.d = (T*)p;
+    v.ld = ld;
+    return v;
+  }
+  v.d = ar.get<T>((size_t)m * n);
+  v.ld = m;
+  ZCSD_CUDA(cudaMemcpy2DAsync(v.d, sizeof(T) * m, p, sizeof(T) * ld, sizeof(T) * m, n, cudaMemcpyHostToDevice,
+                              cx.stream));
+  return v;
+}
+
+template <class T>
+Mat<T> view_out(Arena& ar, void* p, int ld, int m, int n) {
+  Mat<T> v;
+  if (is_device_ptr(p)) {
+    v.d = (T*)p;
+    v.ld = ld;
+    return v;
+  }
+  v.d = ar.get<T>((size_t)m * n);
+  v.ld = m;
+  v.host_out = p;
+  v.host_ld = ld;
+  return v;
+}
+
+template <class T>
+void copy_out(Ctx& cx, const Mat<T>& v, int m, int n) {
+  if (!v.host_out) return;
+  ZCSD_CUDA(cudaMemcpy2DAsync(v.host_out, sizeof(T) * v.host_ld, v.d, sizeof(T) * m, sizeof(T) * m, n,
+                              cudaMemcpyDeviceToHost, cx.stream));
+}
+
+template <class T>
+int csd_typed(csd_ctx* ctx, int n, const void* A1, int lda1, const void* A2, int lda2, void* U1, int ldu1, void* U2,
+              int ldu2, void* V1, int ldv1, double* theta, int* rank, csd_info* info) {
+  Ctx& cx = ctx->cx;
+  const size_t need = csd_bytes(n, sizeof(T)) + (size_t)8 * n * n * sizeof(T);
+  return run_with_ws(cx, need, info, [&](Arena& ar) -> int {
+    Mat<T> a1 = view_in<T>(cx, ar, A1, lda1, n, n);
+    Mat<T> a2 = view_in<T>(cx, ar, A2, lda2, n, n);
+    Mat<T> u1 = view_out<T>(ar, U1, ldu1, n, n);
+    Mat<T> u2 = view_out<T>(ar, U2, ldu2, n, n);
+    Mat<T> v1 = view_out<T>(ar, V1, ldv1, n, n);
+    Mat<double> th = view_out<double>(ar, theta, n, n, 1);
+    int rk = 0;
+    int st = csd_impl<T>(cx, ar, n, a1.d, a1.ld, a2.d, a2.ld, u1.d, u1.ld, u2.d, u2.ld, v1.d, v1.ld, th.d, &rk, info);
+    if (st == CSD_OK || st == CSD_WARN_ALG2_RCHECK) {
+      copy_out(cx, u1, n, n);
+      copy_out(cx, u2, n, n);
+      copy_out(cx, v1, n, n);
+      copy_out(cx, th, n, 1);
+      ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+      if (rank) *rank = rk;
+    }
+    return st;
+  });
+}
+
+template <class T>
+int polar_typed(csd_ctx* ctx, int n, const void* A, int lda, void* W, int ldw, void* H, int ldh, csd_info* info) {
+  Ctx& cx = ctx->cx;
+  const size_t need = polar_bytes(n, 1, sizeof(T)) + (size_t)8 * n * n * sizeof(T);
+  return run_with_ws(cx, need, info, [&](Arena& ar) -> int {
+    Mat<T> a = view_in<T>(cx, ar, A, lda, n, n);
+    Mat<T> w = view_out<T>(ar, W, ldw, n, n);
+    Mat<T> h;
+    if (H) h = view_out<T>(ar, H, ldh, n, n);
+    int st = polar_impl<T>(cx, ar, n, a.d, a.ld, w.d, w.ld, H ? h.d : nullptr, h.ld, info);
+    if (st == CSD_OK) {
+      copy_out(cx, w, n, n);
+      if (H) copy_out(cx, h, n, n);
+      ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+    }
+    return st;
+  });
+}
+
+template <class T>
+int heig_typed(csd_ctx* ctx, int n, const void* B, int ldb, double* lam, void* V, int ldv, csd_info* info) {
+  Ctx& cx = ctx->cx;
+  const size_t need = heig_bytes(n, sizeof(T)) + (size_t)4 * n * n * sizeof(T);
+  return run_with_ws(cx, need, info, [&](Arena& ar) -> int {
+    Mat<T> b = view_in<T>(cx, ar, B, ldb, n, n);
+    Mat<T> v = view_out<T>(ar, V, ldv, n, n);
+    Mat<double> l = view_out<double>(ar, lam, n, n, 1);
+    int st = heig_entry<T>(cx, ar, n, b.d, b.ld, l.d, v.d, v.ld, info);
+    if (st == CSD_OK) {
+      copy_out(cx, v, n, n);
+      copy_out(cx, l, n, 1);
+      ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+    }
+    return st;
+  });
+}
+
+}  // namespace
+
+extern "C" {
+
+int csd_create(csd_ctx** ctx, int device, void* stream) {
+  if (!ctx) return -1;
+  int cnt = 0;
+  if (cudaGetDeviceCount(&cnt) != cudaSuccess || cnt <= 0) {
+    cudaGetLastError();
+    return CSD_ERR_NO_DEVICE;
+  }
+  if (device < 0 || device >= cnt) return -2;
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return CSD_ERR_CUDA; }
+  csd_ctx* c = new (std::nothrow) csd_ctx();
+  if (!c) return CSD_ERR_ALLOC;
+  c->cx.device = device;
+  c->cx.stream = (cudaStream_t)stream;
+  if (cudaMallocHost((void**)&c->cx.hs.d, 64 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->cx.hs.i, 4096 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return CSD_ERR_ALLOC;
+  }
+  *ctx = c;
+  return CSD_OK;
+}
+
+int csd_set_stream(csd_ctx* ctx, void* stream) {
+  if (!ctx) return -1;
+  ctx->cx.stream = (cudaStream_t)stream;
+  return CSD_OK;
+}
+
+int csd_destroy(csd_ctx* ctx) {
+  if (!ctx) return CSD_OK;
+  cudaSetDevice(ctx->cx.device);
+  cudaStreamSynchronize(ctx->cx.stream);
+  if (ctx->cx.ws) cudaFree(ctx->cx.ws);
+  if (ctx->cx.hs.d) cudaFreeHost(ctx->cx.hs.d);
+  if (ctx->cx.hs.i) cudaFreeHost(ctx->cx.hs.i);
+  delete ctx;
+  return CSD_OK;
+}
+
+long long csd_workspace_bytes(const csd_ctx* ctx) { return ctx ? (long long)ctx->cx.ws_bytes : 0; }
+
+long long csd_launch_count(void) { return launch_count(); }
+
+int csd_profile_enable(csd_ctx* ctx, int enable) {
+  if (!ctx) return -1;
+  try {
+    cudaSetDevice(ctx->cx.device);
+    ctx->cx.prof.flush();
+    ctx->cx.prof.reset();
+  } catch (CudaFail&) {
+    return CSD_ERR_CUDA;
+  }
+  ctx->cx.prof.enabled = enable != 0;
+  return CSD_OK;
+}
+
+int csd_profile_read(csd_ctx* ctx, csd_profile* out) {
+  if (!ctx) return -1;
+  if (!out) return -2;
+  try {
+    cudaSetDevice(ctx->cx.device);
+    ctx->cx.prof.flush();
+  } catch (CudaFail&) {
+    return CSD_ERR_CUDA;
+  }
+  for (int k = 0; k < PK_KINDS; ++k) {
+    out->count[k] = ctx->cx.prof.count[k];
+    out->ms[k] = ctx->cx.prof.ms[k];
+    out->flops[k] = ctx->cx.prof.flops[k];
+  }
+  return CSD_OK;
+}
+
+int csd_polar(csd_ctx* ctx, int dtype, int n, const void* A1, int lda1, const void* A2, int lda2, void* U1, int ldu1,
+              void* U2, int ldu2, void* V1, int ldv1, double* theta, int* rank, csd_info* info) {
+  if (!ctx) return -1;
+  if (dtype != CSD_F64 && dtype != CSD_C128) return -2;
+  if (n < 1) return -3;
+  if (!A1) return -4;
+  if (lda1 < n) return -5;
+  if (!A2) return -6;
+  if (lda2 < n) return -7;
+  if (!U1) return -8;
+  if (ldu1 < n) return -9;
+  if (!U2) return -10;
+  if (ldu2 < n) return -11;
+  if (!V1) return -12;
+  if (ldv1 < n) return -13;
+  if (!theta) return -14;
+  if (info) std::memset(info, 0, sizeof(csd_info));
+  if (dtype == CSD_F64)
+    return csd_typed<double>(ctx, n, A1, lda1, A2, lda2, U1, ldu1, U2, ldu2, V1, ldv1, theta, rank, info);
+  return csd_typed<z64>(ctx, n, A1, lda1, A2, lda2, U1, ldu1, U2, ldu2, V1, ldv1, theta, rank, info);
+}
+
+int polar(csd_ctx* ctx, int dtype, int n, const void* A, int lda, void* W, int ldw, void* H, int ldh,
+          csd_info* info) {
+  if (!ctx) return -1;
+  if (dtype != CSD_F64 && dtype != CSD_C128) return -2;
+  if (n < 1) return -3;
+  if (!A) return -4;
+  if (lda < n) return -5;
+  if (!W) return -6;
+  if (ldw < n) return -7;
+  if (H && ldh < n) return -9;
+  if (info) std::memset(info, 0, sizeof(csd_info));
+  if (dtype == CSD_F64) return polar_typed<double>(ctx, n, A, lda, W, ldw, H, ldh, info);
+  return polar_typed<z64>(ctx, n, A, lda, W, ldw, H, ldh, info);
+}
+
+int heig(csd_ctx* ctx, int dtype, int n, const void* B, int ldb, double* lambda, void* V, int ldv, csd_info* info) {
+  if (!ctx) return -1;
+  if (dtype != CSD_F64 && dtype != CSD_C128) return -2;
+  if (n < 1) return -3;
+  if (!B) return -4;
+  if (ldb < n) return -5;
+  if (!lambda) return -6;
+  if (!V) return -7;
+  if (ldv < n) return -8;
+  if (info) std::memset(info, 0, sizeof(csd_info));
+  if (dtype == CSD_F64) return heig_typed<double>(ctx, n, B, ldb, lambda, V, ldv, info);
+  return heig_typed<z64>(ctx, n, B, ldb, lambda, V, ldv, info);
+}
+
+const char* csd_status_str(int s) {
+  if (s < 0) return "invalid argument";
+  switch (s) {
+    case CSD_OK: return "ok";
+    case CSD_ERR_CUDA: return "CUDA error";
+    case CSD_ERR_NOT_CONVERGED: return "Zolo-pd did not converge";
+    case CSD_WARN_ALG2_RCHECK: return "Algorithm 2 check ||R~ - R|| above tolerance (outputs written)";
+    case CSD_ERR_EIG_SPLIT: return "Zolo-eig could not split a block";
+    case CSD_ERR_NONFINITE: return "input holds NaN or Inf";
+    case CSD_ERR_ALLOC: return "device workspace allocation failed";
+    case CSD_ERR_INTERNAL: return "internal error";
+    case CSD_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"
