@@ -284,19 +284,22 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
     // against ||B||_F of the whole matrix, which is what the backward error
     // of the eigendecomposition is relative to.
     const double scal_tol = 100.0 * U_ROUND * bnorm * std::sqrt((double)sz);
-    const double off_tol = 20.0 * U_ROUND * bnorm * std::sqrt((double)sz);
+    const double off_tol = 50.0 * U_ROUND * bnorm * std::sqrt((double)sz);
     const double s0 = s;
+    double spread = 0.0;  // ||B_sub - s0 I||_F / sqrt(sz): RMS distance of the eigenvalues from s0
     for (int attempt = 0; attempt < 7 && !done; ++attempt) {
       if (attempt > 0) {
         ed->retries += 1;
-        // shifts s0 + (+1, -1, +2, -2, +4, -4) * 1e-3 ||B_sub||_F / sqrt(sz)
+        // shifts s0 + (+1, -1, +2, -2, +4, -4) * 0.05 * spread: stay inside the
+        // block's spectrum, which may be a cluster much narrower than ||B_sub||
         const double mag = (double)(1 << ((attempt - 1) / 2)) * (attempt & 1 ? 1.0 : -1.0);
-        s = s0 + 1e-3 * mag * bsub_norm / std::sqrt((double)sz);
+        s = s0 + 0.05 * mag * spread;
       }
       // X = (B - sI) / ||B - sI||_F
       fro2<T>(st, sz, sz, Bsub, n, 0, s, sc + 2, 1, scratch);
       d2h(cx, cx.hs.d, sc + 2, sizeof(double));
       const double xnorm = std::sqrt(cx.hs.d[0]);
+      if (attempt == 0) spread = xnorm / std::sqrt((double)sz);
       if (xnorm <= scal_tol) {
         // B_sub = sI to working precision: every vector is an eigenvector
         if (bk.top && restricted) lo = (s < split_at) ? off : off + sz;
@@ -338,18 +341,20 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
         qr_form_q<T>(st, ar, q, Qf, sz, 0);
         ar.release(mq);
       }
-      // B' = Q^* B_sub Q
-      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Bsub, n, Qf, sz, zer, Tmp, sz);
-      gemm1<T>(st, OP_C, OP_N, sz, sz, sz, one, Qf, sz, Tmp, sz, zer, Xs, sz);
-      fro2<T>(st, sz - k, k, Xs + k, sz, 0, 0.0, sc + 6, 1, scratch);
+      // B' = Q^* B_sub Q = ||B_sub - sI||_F Q^* X Q + s I: the shift is added
+      // back exactly, so the departure of Q from orthogonality is multiplied
+      // by the small ||B_sub - sI|| (not by |s|) in the off-diagonal block
+      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Xs, sz, Qf, sz, zer, Tmp, sz);
+      gemm1<T>(st, OP_C, OP_N, sz, sz, sz, from_re<T>(xnorm), Qf, sz, Tmp, sz, zer, Om, sz);
+      fro2<T>(st, sz - k, k, Om + k, sz, 0, 0.0, sc + 6, 1, scratch);
       d2h(cx, cx.hs.d, sc + 6, sizeof(double));
       const double offa = std::sqrt(cx.hs.d[0]);
       if (debug) fprintf(stderr, "zolo-eig:   k=%d ||B21||=%.3e tol=%.3e\n", k, offa, off_tol);
       if (!(offa <= off_tol)) continue;
       ed->offblock = std::max(ed->offblock, offa / std::max(bnorm, 1e-300));
       ed->splits += 1;
-      // accept: B_sub <- B', V[:, off:off+sz] <- V[:, off:off+sz] Q
-      axpby<T>(st, sz, sz, 1.0, Xs, sz, 0, 0.0, Bsub, n, 0, 1);
+      // accept: B_sub <- B' (+ s I), V[:, off:off+sz] <- V[:, off:off+sz] Q
+      copy_shift<T>(st, sz, 1.0, Om, sz, 0, s, Bsub, n, 0, 1);
       gemm1<T>(st, OP_N, OP_N, n, sz, sz, one, V + (long long)off * n, n, Qf, sz, zer, Tmp, n);
       axpby<T>(st, n, sz, 1.0, Tmp, n, 0, 0.0, V + (long long)off * n, n, 0, 1);
       if (bk.top && restricted) {
