@@ -113,6 +113,29 @@ int polar(csd_ctx* ctx, int dtype, int n, const void* A, int lda,
 int heig(csd_ctx* ctx, int dtype, int n, const void* B, int ldb,
          double* lambda, void* V, int ldv, csd_info* info);
 
+/* polar() without any allocation, for callers that cannot allocate device
+ * memory: code running where cudaMalloc is unavailable or forbidden (for
+ * instance inside a host callback or a memory-budgeted plug-in whose
+ * allocations must all be made up front), or that must not add memory while
+ * another component owns the device.  The paper has no counterpart: it is a
+ * deployment variant of the Zolo-pd entry point.
+ *   - n <= CSD_NOALLOC_MAX_N (64); a larger n returns -2.
+ *   - A, W and H (H may be NULL) must be device pointers; a host pointer
+ *     returns -3 / -5 / -7.  `stream` is a cudaStream_t (NULL = legacy default
+ *     stream).  The call synchronises that stream before returning.
+ *   - Scratch memory is one static device array of 6 MiB inside this library,
+ *     which every GPU that loads the library holds until the process exits.
+ *     The first call on a device looks up that array's device address (no
+ *     allocation); make that first call before any stream capture.
+ *   - The call calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - Every call shares the one scratch array and starts by writing all the
+ *     scratch it reads, so nothing is carried over from the previous call;
+ *     calls that overlap on the GPU (other threads or streams, same device)
+ *     race on it and must be serialised by the caller.
+ * Same results and status codes as polar() otherwise. */
+#define CSD_NOALLOC_MAX_N 64
+int polar_noalloc(int dtype, int n, const void* A, int lda, void* W, int ldw, void* H, int ldh, void* stream);
+
 /* Zolotarev coefficients for [ell, 1] and r terms (host only, no GPU):
  * c[0..2r-1] = c_1..c_2r, a[0..r-1] = a_1..a_r, *mhat (Z(1) = 1) and
  * *ell_next = Z(ell).  0 < ell < 1, 1 <= r <= 16.  Returns 0 or -k. */

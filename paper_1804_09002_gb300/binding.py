@@ -69,6 +69,7 @@ def _load():
                               ctypes.POINTER(ci), ctypes.POINTER(csd_info)]
     lib.polar.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, ctypes.POINTER(csd_info)]
     lib.heig.argtypes = [vp, ci, ci, vp, ci, vp, vp, ci, ctypes.POINTER(csd_info)]
+    lib.polar_noalloc.argtypes = [ci, ci, vp, ci, vp, ci, vp, ci, vp]
     lib.zolo_coeffs.argtypes = [cd, ci, vp, vp, ctypes.POINTER(cd), ctypes.POINTER(cd)]
     lib.zolo_plan.argtypes = [cd, ci, ci, vp, vp]
     lib.csd_profile_enable.argtypes = [vp, ci]
@@ -78,7 +79,7 @@ def _load():
     lib.csd_status_str.argtypes = [ci]
     lib.csd_status_str.restype = ctypes.c_char_p
     for f in ("csd_create", "csd_set_stream", "csd_destroy", "csd_polar", "polar", "heig", "zolo_coeffs",
-              "zolo_plan", "csd_profile_enable", "csd_profile_read"):
+              "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc"):
         getattr(lib, f).restype = ci
     return lib
 
@@ -87,7 +88,7 @@ lib = _load()
 
 EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes", "csd_polar", "polar", "heig",
             "zolo_coeffs", "zolo_plan", "csd_status_str", "csd_profile_enable", "csd_profile_read",
-            "csd_launch_count"]
+            "csd_launch_count", "polar_noalloc"]
 
 
 class CSDError(RuntimeError):

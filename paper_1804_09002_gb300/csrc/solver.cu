@@ -7,14 +7,10 @@
 #include <vector>
 
 #include "../../include/zolo_csd.h"
-#include "linalg.h"
-#include "profile.h"
+#include "solver.h"
 
 namespace zcsd {
 
-constexpr double U_ROUND = 0x1p-53;
-constexpr double EPS_ZOLO = 1e-15;  // interval [eps, 1] of the modified Zolo-pd (Section 5.1)
-constexpr int R_MAX = 8;            // p <= 8 (Section 5)
 
 // ---------------------------------------------------------------- small kernels
 namespace {
@@ -77,27 +73,7 @@ int grid_for(long long total) { return (int)std::min<long long>((total + 255) / 
 
 }  // namespace
 
-// ---------------------------------------------------------------- context
-struct Plan {
-  int steps = 0;
-  int r[4];
-  double ell[4];
-  double c[4][2 * R_MAX], a[4][R_MAX], mhat[4], sqrtc[4][R_MAX], w[4][R_MAX];
-};
-
-struct Ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  HostScalars hs;
-  Plan plan;
-  bool plan_ready = false;
-  unsigned long long seed = 0x5EEDull;
-  Profiler prof;
-};
-
-static const Plan& get_plan(Ctx& cx) {
+const Plan& get_plan(Ctx& cx) {
   if (!cx.plan_ready) {
     Plan& p = cx.plan;
     p.steps = zolo_plan(EPS_ZOLO, R_MAX, 4, p.r, p.ell);
@@ -114,15 +90,12 @@ static const Plan& get_plan(Ctx& cx) {
   return cx.plan;
 }
 
-static void d2h(Ctx& cx, void* dst, const void* src, size_t bytes) {
+void d2h(Ctx& cx, void* dst, const void* src, size_t bytes) {
   ZCSD_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, cx.stream));
   ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
 }
 
 // ---------------------------------------------------------------- Zolo-pd
-struct PolarDiag {
-  int chol_fallback = 0;
-};
 
 // W_p = Zolo-pd polar factor of X0_p (p < P), X0 with ||X0_p||_2 <= 1 (ld n,
 // stride n*n).  W may alias nothing else.  Section 5: iterates
@@ -214,6 +187,9 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd)
   axpby<T>(st, n, n, 1.0, X, n, nn, 0.0, W, n, nn, P);
   ar.release(mk);
 }
+
+template void zolo_pd<double>(Ctx&, Arena&, int, int, const double*, double*, PolarDiag*);
+template void zolo_pd<z64>(Ctx&, Arena&, int, int, const z64*, z64*, PolarDiag*);
 
 // ---------------------------------------------------------------- Zolo-eig
 struct EigDiag {
