@@ -11,7 +11,8 @@ remark (iii), written out step by step in FP64 with *independent* sub-solvers:
 Readings taken where the paper leaves a choice (listed in the design doc):
   * rank r = round(||A||_F^2) and mu = 0 if r = n else 2 (remark (vi), line 3);
   * H_i symmetrised as (H + H^*)/2 (Theorem 3.1 assumes H Hermitian);
-  * theta = atan2(S, C) (remark (iii), arctan(S/C) read with quadrant);
+  * theta = atan2(S, C) (remark (iii), arctan(S/C) read with quadrant),
+    clamped to [0, pi/2], the range of the principal angles (Section 1);
   * angles returned ascending (Section 1 orders 0 <= theta_1 <= ... );
   * for mu = 2 the eigenvalues with Lambda <= 1.5 are kept (Algorithm 3,
     line 5 keeps those in [-1, 1]; the others sit at mu = 2).
@@ -112,8 +113,10 @@ def csd(A1, A2, mu=None):
     U2 = W2 @ V
     C = np.real(np.einsum("ij,ij->j", V.conj(), H1 @ V))
     S = np.real(np.einsum("ij,ij->j", V.conj(), H2 @ V))
-    # remark (iii): theta = arctan(S/C), then C = cos(theta), S = sin(theta)
-    theta = np.arctan2(S, C)
+    # remark (iii): theta = arctan(S/C), then C = cos(theta), S = sin(theta);
+    # the principal angles lie in [0, pi/2] (Section 1), so rounding below 0
+    # or above pi/2 is clamped
+    theta = np.clip(np.arctan2(S, C), 0.0, np.pi / 2)
     order = np.argsort(theta, kind="stable")
     theta = theta[order]
     U1, U2, V = U1[:, order], U2[:, order], V[:, order]
