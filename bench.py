@@ -230,7 +230,8 @@ def main():
     num = torch.sqrt(torch.linalg.norm(A1 - (U1 * c) @ V1.T) ** 2 + torch.linalg.norm(A2 - (U2 * s_) @ V1.T) ** 2)
     bwd = float(num / np.sqrt(2.0 * n))  # ||A||_F = sqrt(n) per block for orthonormal columns
     ang = float(np.max(np.abs(th.cpu().numpy() - th_known)))
-    orth = max(float(torch.linalg.norm(X.T @ X - torch.eye(rk, device=dev, dtype=X.dtype), 2)) for X in (U1, U2, V1))
+    # Frobenius norm (a plain reduction; the 2-norm would need torch's solver library)
+    orth = max(float(torch.linalg.norm(X.T @ X - torch.eye(rk, device=dev, dtype=X.dtype))) for X in (U1, U2, V1))
     # ---- e2e: same call with pinned host buffers (copies inside the call)
     e2e = None
     if args.e2e_steps > 0:
@@ -266,11 +267,15 @@ def main():
                                f"1/4 within 1e-8 of pi/2), 1e-14 noise, re-orthonormalised",
                    "n": n, "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (2 x 128 MiB)"},
         "accuracy": {"max_abs_theta_err_vs_known": ang, "backward_err_fro_over_u": bwd / U,
-                     "orth_over_u": orth / U, "rank": rk},
+                     "orth_fro_over_u": orth / U, "rank": rk},
         "roofline": {"kernel": kinds[dom], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"},
         "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "gemm_sites": {nm: {"ms_per_step": prof.site_ms[i] / args.steps,
+                            "tflops": prof.site_flops[i] / max(prof.site_ms[i], 1e-9) / 1e9,
+                            "launches_per_step": prof.site_count[i] / args.steps}
+                       for i, nm in enumerate(B.csd_profile.SITES) if prof.site_count[i]},
         "clocks": ck, "gpu_launches": int(launches),
     }
     if e2e:

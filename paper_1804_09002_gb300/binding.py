@@ -52,7 +52,13 @@ class csd_info(ctypes.Structure):
 
 
 class csd_profile(ctypes.Structure):
-    _fields_ = [("count", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4), ("flops", ctypes.c_double * 4)]
+    _fields_ = [("count", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4), ("flops", ctypes.c_double * 4),
+                ("site_count", ctypes.c_longlong * 24), ("site_ms", ctypes.c_double * 24),
+                ("site_flops", ctypes.c_double * 24)]
+
+    SITES = ["other", "qr_W", "qr_W2", "qr_update", "formq_W", "formq_W2", "formq_update", "zolo_combine",
+             "gram", "chol_row", "chol_trailing", "trsm_f_update", "trsm_f_diag", "trsm_b_update",
+             "trsm_b_diag", "H", "orth", "eig", "assembly", "alg2"]
 
 
 def _load():

@@ -13,15 +13,26 @@ namespace zcsd {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
-template <class T, int OPA, int OPB>
-__global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
-  const int b = blockIdx.z;
+// Output tile BM x BN (BM * BN = 4096: 16 outputs per thread as a 4 x 4
+// register tile), k-step BK.  BM = 64 (64 x 64 tiles) is the default; BM = 32
+// (32 x 128 tiles) serves the m <= 32 products of the compact-WY updates.
+template <class T, int OPA, int OPB, int BM>
+__global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<T> g) {
+  constexpr int BN = 4096 / BM;
+  constexpr int TX = BM / 4, TY = BN / 4;  // thread grid over the tile
+  const int z = blockIdx.z;
+  const int b = z / g.ksplit, ks = z % g.ksplit;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   if (g.uplo == 1 && m0 > n0 + BN - 1) return;
   if (g.uplo == 2 && n0 > m0 + BM - 1) return;
   int kb = 0, ke = g.k;
+  if (g.ksplit > 1) {
+    const int kc = ((g.k + g.ksplit - 1) / g.ksplit + BK - 1) / BK * BK;
+    kb = ks * kc;
+    ke = min(g.k, kb + kc);
+  }
   if (g.kflags & K_FROM_COL) kb = max(kb, n0);
   if (g.kflags & K_FROM_ROW) kb = max(kb, m0);
   if (g.kflags & K_TO_COL) ke = min(ke, n0 + BN);
@@ -30,7 +41,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tx = tid % TX, ty = tid / TX;
   T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -42,64 +53,48 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
     const T* B = g.B + (b / g.bdivB) * g.sB + js * g.sBj;
     const double wj = g.w[js];
     for (int kt = (kb / BK) * BK; kt < ke; kt += BK) {
-      // ---- load op(A)[m0:m0+BM, kt:kt+BK] into As[k][i]
-      if (OPA == OP_N) {
-        const int i = tid & 63;
+      // ---- op(A)[m0:m0+BM, kt:kt+BK] -> As[k][i], coalesced along memory
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int k = (tid >> 6) + 4 * s;
-          const int gi = m0 + i, gk = kt + k;
-          T v = zero<T>();
-          if (gi < g.m && gk >= kb && gk < ke) v = A[gi + (long long)gk * g.lda];
-          As[k][i] = scal(wj, v);
-        }
-      } else {
-        const int k = tid & 15;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int i = (tid >> 4) + 16 * s;
-          const int gi = m0 + i, gk = kt + k;
-          T v = zero<T>();
-          if (gi < g.m && gk >= kb && gk < ke) {
+      for (int s = 0; s < (BM * BK) / NT; ++s) {
+        const int e = tid + NT * s;
+        const int i = (OPA == OP_N) ? (e % BM) : (e / BK);
+        const int k = (OPA == OP_N) ? (e / BM) : (e % BK);
+        const int gi = m0 + i, gk = kt + k;
+        T v = zero<T>();
+        if (gi < g.m && gk >= kb && gk < ke) {
+          if (OPA == OP_N) v = A[gi + (long long)gk * g.lda];
+          else {
             v = A[gk + (long long)gi * g.lda];
             if (OPA == OP_C) v = conj_(v);
           }
-          As[k][i] = scal(wj, v);
         }
+        As[k][i] = scal(wj, v);
       }
-      // ---- load op(B)[kt:kt+BK, n0:n0+BN] into Bs[k][j]
-      if (OPB == OP_N) {
-        const int k = tid & 15;
+      // ---- op(B)[kt:kt+BK, n0:n0+BN] -> Bs[k][j]
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int j = (tid >> 4) + 16 * s;
-          const int gj = n0 + j, gk = kt + k;
-          T v = zero<T>();
-          if (gj < g.n && gk >= kb && gk < ke) v = B[gk + (long long)gj * g.ldb];
-          Bs[k][j] = v;
-        }
-      } else {
-        const int j = tid & 63;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int k = (tid >> 6) + 4 * s;
-          const int gj = n0 + j, gk = kt + k;
-          T v = zero<T>();
-          if (gj < g.n && gk >= kb && gk < ke) {
+      for (int s = 0; s < (BN * BK) / NT; ++s) {
+        const int e = tid + NT * s;
+        const int k = (OPB == OP_N) ? (e % BK) : (e / BN);
+        const int j = (OPB == OP_N) ? (e / BK) : (e % BN);
+        const int gj = n0 + j, gk = kt + k;
+        T v = zero<T>();
+        if (gj < g.n && gk >= kb && gk < ke) {
+          if (OPB == OP_N) v = B[gk + (long long)gj * g.ldb];
+          else {
             v = B[gj + (long long)gk * g.ldb];
             if (OPB == OP_C) v = conj_(v);
           }
-          Bs[k][j] = v;
         }
+        Bs[k][j] = v;
       }
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < BK; ++k) {
         T a[4], bb[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
+        for (int i = 0; i < 4; ++i) a[i] = As[k][tx + TX * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bb[j] = Bs[k][ty + 16 * j];
+        for (int j = 0; j < 4; ++j) bb[j] = Bs[k][ty + TY * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -109,16 +104,16 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
     }
   }
   // ---- epilogue
-  T* C = g.C + b * g.sC;
+  T* C = g.C + z * g.sC;
   const T* Cin = g.Cin ? g.Cin + (b / g.bdivC) * g.sCin : nullptr;
-  const bool use_beta = Cin && (re(g.beta) != 0.0 || im(g.beta) != 0.0);
+  const bool use_beta = Cin && ks == 0 && (re(g.beta) != 0.0 || im(g.beta) != 0.0);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int gj = n0 + ty + 16 * j;
+    const int gj = n0 + ty + TY * j;
     if (gj >= g.n) continue;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int gi = m0 + tx + 16 * i;
+      const int gi = m0 + tx + TX * i;
       if (gi >= g.m) continue;
       T v = mul(g.alpha, acc[i][j]);
       if (use_beta) v = fmac(g.beta, Cin[gi + (long long)gj * g.ldcin], v);
@@ -127,19 +122,30 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
   }
 }
 
-template <class T, int OPA>
-void gemm_dispatch_b(const GemmArgs<T>& g, dim3 grid, cudaStream_t st) {
+template <class T, int OPA, int BM>
+void gemm_dispatch_b(const GemmArgs<T>& g, cudaStream_t st) {
+  constexpr int BN = 4096 / BM;
+  dim3 grid(ceil_div(g.m, BM), ceil_div(g.n, BN), g.batch * g.ksplit);
   switch (g.opB) {
-    case OP_N: gemm_kernel<T, OPA, OP_N><<<grid, NT, 0, st>>>(g); break;
-    case OP_T: gemm_kernel<T, OPA, OP_T><<<grid, NT, 0, st>>>(g); break;
-    default: gemm_kernel<T, OPA, OP_C><<<grid, NT, 0, st>>>(g); break;
+    case OP_N: gemm_kernel<T, OPA, OP_N, BM><<<grid, NT, 0, st>>>(g); break;
+    case OP_T: gemm_kernel<T, OPA, OP_T, BM><<<grid, NT, 0, st>>>(g); break;
+    default: gemm_kernel<T, OPA, OP_C, BM><<<grid, NT, 0, st>>>(g); break;
+  }
+}
+
+template <class T, int BM>
+void gemm_dispatch(const GemmArgs<T>& g, cudaStream_t st) {
+  switch (g.opA) {
+    case OP_N: gemm_dispatch_b<T, OP_N, BM>(g, st); break;
+    case OP_T: gemm_dispatch_b<T, OP_T, BM>(g, st); break;
+    default: gemm_dispatch_b<T, OP_C, BM>(g, st); break;
   }
 }
 
 // Multiply-add work the kernel executes for g, counted per output tile over
 // the k range it traverses (2 flops per real FMA, 8 per complex FMA).
 template <class T>
-double gemm_flops(const GemmArgs<T>& g) {
+double gemm_flops(const GemmArgs<T>& g, int BM, int BN) {
   double fma = 0.0;
   const int tm = ceil_div(g.m, BM), tn = ceil_div(g.n, BN);
   for (int bx = 0; bx < tm; ++bx) {
@@ -164,24 +170,19 @@ double gemm_flops(const GemmArgs<T>& g) {
 template <class T>
 void gemm(const GemmArgs<T>& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return;
-  dim3 grid(ceil_div(g.m, BM), ceil_div(g.n, BN), g.batch);
-  if (g.k <= 0 || g.nsum <= 0) {
-    // C = beta * Cin (no product): reuse the kernel with an empty k loop
-  }
+  const bool narrow = g.m <= 32;
   ProfToken tok = prof_begin(st);
-  switch (g.opA) {
-    case OP_N: gemm_dispatch_b<T, OP_N>(g, grid, st); break;
-    case OP_T: gemm_dispatch_b<T, OP_T>(g, grid, st); break;
-    default: gemm_dispatch_b<T, OP_C>(g, grid, st); break;
-  }
+  if (narrow) gemm_dispatch<T, 32>(g, st);
+  else gemm_dispatch<T, 64>(g, st);
   ZCSD_LAUNCH();
-  if (tok.slot >= 0) prof_end(tok, st, PK_GEMM, gemm_flops(g));
+  if (tok.slot >= 0) prof_end(tok, st, PK_GEMM, narrow ? gemm_flops(g, 32, 128) : gemm_flops(g, 64, 64), g.site);
 }
 
 template <class T>
 void gemm1(cudaStream_t st, int opA, int opB, int m, int n, int k, T alpha, const T* A, int lda,
-           const T* B, int ldb, T beta, T* C, int ldc, int uplo, int kflags) {
+           const T* B, int ldb, T beta, T* C, int ldc, int uplo, int kflags, int site) {
   GemmArgs<T> g;
+  g.site = site;
   g.m = m; g.n = n; g.k = k; g.opA = opA; g.opB = opB;
   g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
   g.Cin = C; g.ldcin = ldc; g.C = C; g.ldc = ldc;
@@ -430,9 +431,11 @@ __global__ void sum_vec_kernel(int n, const double* d, double* out) {
   if (threadIdx.x == 0) *out = r;
 }
 
+// theta = atan2(S, C) clamped to [0, pi/2], the range of the principal
+// angles (Section 1); rounding can otherwise leave S or C a few ulps below 0.
 __global__ void theta_kernel(int n, const double* C, const double* S, double* th) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    th[i] = atan2(S[i], C[i]);
+    th[i] = fmin(fmax(atan2(S[i], C[i]), 0.0), 1.5707963267948966);
 }
 
 // rank of each key among all keys (ties by index): perm[rank] = index.
@@ -591,7 +594,7 @@ void randn(cudaStream_t st, int m, int n, T* X, int ldx, unsigned long long seed
 #define ZCSD_INST(T)                                                                                             \
   template void gemm<T>(const GemmArgs<T>&, cudaStream_t);                                                      \
   template void gemm1<T>(cudaStream_t, int, int, int, int, int, T, const T*, int, const T*, int, T, T*, int, int, \
-                         int);                                                                                  \
+                         int, int);                                                                                \
   template void axpby<T>(cudaStream_t, int, int, double, const T*, int, long long, double, T*, int, long long, int); \
   template void copy_shift<T>(cudaStream_t, int, double, const T*, int, long long, double, T*, int, long long, int); \
   template void shift_terms<T>(cudaStream_t, int, const T*, int, long long, const double*, int, T*, int, long long, \

@@ -90,7 +90,8 @@ struct ProfToken {
   int slot = -1;
 };
 ProfToken prof_begin(cudaStream_t st);
-void prof_end(ProfToken t, cudaStream_t st, int kind, double flops);
+void prof_end(ProfToken t, cudaStream_t st, int kind, double flops, int site = 0);
+constexpr int PROF_SITES = 24;
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 

@@ -6,6 +6,8 @@
 // everything with O(n^3) work around them is a GEMM (blas.cu).
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "ops.h"
 
 namespace zcsd {
@@ -15,26 +17,44 @@ namespace {
 constexpr int PANEL_THREADS = 512;
 constexpr int PANEL_MAXNB = 32;
 
-// Sum `cnt` per-thread values across the CTA; result in red[nwarps*MAXNB + c].
-// The loop over c is fully unrolled so that `vals` stays in registers.
+// Sum the PANEL_MAXNB per-thread values across the CTA; the total of value c
+// lands in red[nwarps * PANEL_MAXNB + c] for c < cnt.  Inside a warp this is a
+// butterfly reduce-scatter: at each of the 5 xor-shuffle steps a lane keeps
+// half of its remaining values and adds the partner's copy of that half
+// (31 shuffles per component instead of 5 per value), after which lane l
+// holds the warp total of value l.
+__device__ inline void warp_reduce_scatter32(double (&v)[PANEL_MAXNB]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16, cnt = 32; o > 0; o >>= 1, cnt >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      if (t < cnt / 2) {
+        const double send = up ? v[t] : v[t + cnt / 2];
+        const double keep = up ? v[t + cnt / 2] : v[t];
+        v[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+  }
+}
+
 template <class T>
 __device__ void block_reduce_vec(T (&vals)[PANEL_MAXNB], int cnt, T* red /* [nwarps+1][PANEL_MAXNB] */) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double x[PANEL_MAXNB];
 #pragma unroll
-  for (int c = 0; c < PANEL_MAXNB; ++c) {
-    if (c < cnt) {
-      double x = re(vals[c]), y = im(vals[c]);
-      for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_down_sync(0xffffffffu, x, o);
-        if constexpr (sizeof(T) != sizeof(double)) y += __shfl_down_sync(0xffffffffu, y, o);
-      }
-      if (lane == 0) {
-        T v;
-        if constexpr (sizeof(T) == sizeof(double)) v = from_re<T>(x);
-        else { z64 z{x, y}; v = *reinterpret_cast<T*>(&z); }
-        red[w * PANEL_MAXNB + c] = v;
-      }
-    }
+  for (int c = 0; c < PANEL_MAXNB; ++c) x[c] = re(vals[c]);
+  warp_reduce_scatter32(x);
+  if constexpr (sizeof(T) == sizeof(double)) {
+    red[w * PANEL_MAXNB + lane] = from_re<T>(x[0]);
+  } else {
+    double y[PANEL_MAXNB];
+#pragma unroll
+    for (int c = 0; c < PANEL_MAXNB; ++c) y[c] = im(vals[c]);
+    warp_reduce_scatter32(y);
+    z64 z{x[0], y[0]};
+    red[w * PANEL_MAXNB + lane] = *reinterpret_cast<T*>(&z);
   }
   __syncthreads();
   if ((int)threadIdx.x < cnt) {
@@ -159,6 +179,318 @@ __global__ void __launch_bounds__(PANEL_THREADS) qr_panel_kernel(int m, int n, i
     const int r = i % nb, c = i / nb;
     Tf[r + c * nb] = Ts[r + c * PANEL_MAXNB];
   }
+}
+
+// Cluster version of the panel: the CL CTAs of a thread-block cluster split
+// the panel rows; per column each CTA reduces its partial dot products, the
+// partials are exchanged through distributed shared memory after one cluster
+// barrier, and every CTA derives the same reflector (fixed summation order).
+// Double-buffered exchange slots make one barrier per column sufficient: a
+// slot is rewritten two columns later, after every CTA has passed the
+// barrier that follows its last read of it.
+constexpr int PANEL_CL = 8;
+constexpr int PANEL_CL_THREADS = 256;
+
+template <class T>
+__global__ void __launch_bounds__(PANEL_CL_THREADS) qr_panel_cluster_kernel(int m, int n, int band, T* Mall, int ldm,
+                                                                            long long sM, int k0, int nb, T* Yall,
+                                                                            int ldy, long long sY, T* Tall,
+                                                                            long long sT) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ T red[(PANEL_CL_THREADS / 32 + 1) * PANEL_MAXNB];
+  __shared__ T part[2][2 * PANEL_MAXNB];  // [slot][partial dots | pivot row]
+  __shared__ T dtot[PANEL_MAXNB], prow[PANEL_MAXNB];
+  __shared__ T wv[PANEL_MAXNB];
+  __shared__ T Ts[PANEL_MAXNB * PANEL_MAXNB];
+  __shared__ T sh_scale, sh_tau, sh_beta;
+  const int rank = (int)cluster.block_rank();
+  const int b = blockIdx.x / PANEL_CL;
+  T* M = Mall + b * sM;
+  T* Y = Yall + b * sY;
+  T* Tf = Tall + b * sT;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int hrows = min(m, k0 + nb - 1 + band) - k0;
+  const int chunk = (hrows + PANEL_CL - 1) / PANEL_CL;
+  const int rlo = k0 + rank * chunk, rhi = k0 + min(hrows, (rank + 1) * chunk);
+  for (int i = tid; i < PANEL_MAXNB * PANEL_MAXNB; i += nt) Ts[i] = zero<T>();
+  __syncthreads();
+
+  for (int j = 0; j < nb; ++j) {
+    const int k = k0 + j;
+    const int rend = min(m, k + band);
+    const int slot = j & 1;
+    // ---- pass 1 over this CTA's rows: d_c = sum_{i>k} conj(M[i,k]) M[i,k0+c]
+    T d[PANEL_MAXNB];
+#pragma unroll
+    for (int c = 0; c < PANEL_MAXNB; ++c) d[c] = zero<T>();
+    const int i0 = max(k + 1, rlo), i1 = min(rend, rhi);
+    for (int i = i0 + tid; i < i1; i += nt) {
+      const T x = M[i + (long long)k * ldm];
+#pragma unroll
+      for (int c = 0; c < PANEL_MAXNB; ++c)
+        if (c < nb) d[c] = add(d[c], cmul(x, M[i + (long long)(k0 + c) * ldm]));
+    }
+    block_reduce_vec(d, nb, red);
+    const T* dloc = red + (nt / 32) * PANEL_MAXNB;
+    const bool owner = (k >= rlo && k < rhi);
+    if (tid < nb) {
+      part[slot][tid] = dloc[tid];
+      part[slot][PANEL_MAXNB + tid] = owner ? M[k + (long long)(k0 + tid) * ldm] : zero<T>();
+    }
+    cluster.sync();
+    // ---- combine the partials of all CTAs (same order everywhere)
+    if (tid < nb) {
+      T sum = zero<T>(), pr = zero<T>();
+      for (int r = 0; r < PANEL_CL; ++r) {
+        const T* rp = cluster.map_shared_rank(&part[slot][0], r);
+        sum = add(sum, rp[tid]);
+        pr = add(pr, rp[PANEL_MAXNB + tid]);  // only the owner's entry is nonzero
+      }
+      dtot[tid] = sum;
+      prow[tid] = pr;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const T alpha = prow[j];
+      const double xnorm2 = re(dtot[j]);
+      T tau, scale, beta;
+      if (xnorm2 == 0.0 && im(alpha) == 0.0) {
+        tau = zero<T>();
+        scale = zero<T>();
+        beta = alpha;
+      } else {
+        const double nrm = sqrt(abs2(alpha) + xnorm2);
+        const double bt = re(alpha) >= 0.0 ? -nrm : nrm;
+        beta = from_re<T>(bt);
+        tau = make_c<T>((bt - re(alpha)) / bt, -im(alpha) / bt);
+        scale = div_(from_re<T>(1.0), sub(alpha, beta));
+      }
+      sh_tau = tau;
+      sh_scale = scale;
+      sh_beta = beta;
+    }
+    __syncthreads();
+    const T tau = sh_tau, scale = sh_scale;
+    if (tid < nb) {
+      const int c = tid;
+      const T mk = prow[c];
+      if (c > j) wv[c] = add(mk, mul(conj_(scale), dtot[c]));
+      else if (c < j) wv[c] = add(conj_(mk), mul(scale, conj_(dtot[c])));
+    }
+    __syncthreads();
+    if (tid < j) {
+      const int r = tid;
+      T s = zero<T>();
+      for (int c = r; c < j; ++c) s = fmac(Ts[r + c * PANEL_MAXNB], wv[c], s);
+      red[r] = mul(from_re<T>(-1.0), mul(tau, s));
+    }
+    __syncthreads();
+    if (tid < j) Ts[tid + j * PANEL_MAXNB] = red[tid];
+    if (tid == 0) Ts[j + j * PANEL_MAXNB] = tau;
+    // ---- pass 2 over this CTA's rows
+    const T ctau = conj_(tau);
+    const int u0 = max(k, rlo);
+    for (int i = u0 + tid; i < i1; i += nt) {
+      T v;
+      if (i == k) v = from_re<T>(1.0);
+      else {
+        v = mul(scale, M[i + (long long)k * ldm]);
+        M[i + (long long)k * ldm] = v;
+      }
+      Y[(i - k0) + (long long)j * ldy] = v;
+      const T cv = mul(ctau, v);
+      for (int c = j + 1; c < nb; ++c) {
+        T* q = M + i + (long long)(k0 + c) * ldm;
+        *q = sub(*q, mul(cv, wv[c]));
+      }
+    }
+    for (int i = rlo + tid; i < rhi; i += nt)
+      if (i < k || i >= rend) Y[(i - k0) + (long long)j * ldy] = zero<T>();
+    __syncthreads();
+    if (tid == 0 && owner) M[k + (long long)k * ldm] = sh_beta;
+  }
+  if (rank == 0)
+    for (int i = tid; i < nb * nb; i += nt) {
+      const int r = i % nb, c = i / nb;
+      Tf[r + c * nb] = Ts[r + c * PANEL_MAXNB];
+    }
+  // no CTA may exit while another can still read its shared memory
+  cluster.sync();
+}
+
+// Shared-memory-resident cluster panel: as qr_panel_cluster_kernel, but each
+// CTA first copies its block of panel rows (all nb columns) into shared
+// memory, runs every column there, and writes R/V and the explicit V panel
+// back once.  Per column only the cluster exchange touches anything but
+// shared memory.  S holds column c of the CTA's rows at S[c * lds + (i - rlo)].
+template <class T, int CL>
+__global__ void __launch_bounds__(PANEL_CL_THREADS) qr_panel_smem_kernel(int m, int n, int band, T* Mall, int ldm,
+                                                                         long long sM, int k0, int nb, T* Yall,
+                                                                         int ldy, long long sY, T* Tall, long long sT,
+                                                                         int chunk) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* S = reinterpret_cast<T*>(dyn_smem);
+  const int lds = chunk;
+  __shared__ T red[(PANEL_CL_THREADS / 32 + 1) * PANEL_MAXNB];
+  __shared__ T part[2][2 * PANEL_MAXNB];
+  __shared__ T dtot[PANEL_MAXNB], prow[PANEL_MAXNB];
+  __shared__ T wv[PANEL_MAXNB];
+  __shared__ T Ts[PANEL_MAXNB * PANEL_MAXNB];
+  __shared__ T sh_scale, sh_tau, sh_beta;
+  const int rank = (int)cluster.block_rank();
+  const int b = blockIdx.x / CL;
+  T* M = Mall + b * sM;
+  T* Y = Yall + b * sY;
+  T* Tf = Tall + b * sT;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int hrows = min(m, k0 + nb - 1 + band) - k0;
+  const int rlo = k0 + rank * chunk, rhi = k0 + min(hrows, (rank + 1) * chunk);
+  for (int i = tid; i < PANEL_MAXNB * PANEL_MAXNB; i += nt) Ts[i] = zero<T>();
+  for (int c = 0; c < nb; ++c)
+    for (int i = rlo + tid; i < rhi; i += nt) S[c * lds + (i - rlo)] = M[i + (long long)(k0 + c) * ldm];
+  __syncthreads();
+
+  for (int j = 0; j < nb; ++j) {
+    const int k = k0 + j;
+    const int rend = min(m, k + band);
+    const int slot = j & 1;
+    T d[PANEL_MAXNB];
+#pragma unroll
+    for (int c = 0; c < PANEL_MAXNB; ++c) d[c] = zero<T>();
+    const int i0 = max(k + 1, rlo), i1 = min(rend, rhi);
+    for (int i = i0 + tid; i < i1; i += nt) {
+      const T x = S[j * lds + (i - rlo)];
+#pragma unroll
+      for (int c = 0; c < PANEL_MAXNB; ++c)
+        if (c < nb) d[c] = add(d[c], cmul(x, S[c * lds + (i - rlo)]));
+    }
+    block_reduce_vec(d, nb, red);
+    const T* dloc = red + (nt / 32) * PANEL_MAXNB;
+    const bool owner = (k >= rlo && k < rhi);
+    if (tid < nb) {
+      part[slot][tid] = dloc[tid];
+      part[slot][PANEL_MAXNB + tid] = owner ? S[tid * lds + (k - rlo)] : zero<T>();
+    }
+    cluster.sync();
+    if (tid < nb) {
+      T vals[CL], prs[CL];
+#pragma unroll
+      for (int r = 0; r < CL; ++r) {  // independent remote loads, summed in rank order
+        const T* rp = cluster.map_shared_rank(&part[slot][0], r);
+        vals[r] = rp[tid];
+        prs[r] = rp[PANEL_MAXNB + tid];
+      }
+      T sum = zero<T>(), pr = zero<T>();
+#pragma unroll
+      for (int r = 0; r < CL; ++r) {
+        sum = add(sum, vals[r]);
+        pr = add(pr, prs[r]);
+      }
+      dtot[tid] = sum;
+      prow[tid] = pr;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const T alpha = prow[j];
+      const double xnorm2 = re(dtot[j]);
+      T tau, scale, beta;
+      if (xnorm2 == 0.0 && im(alpha) == 0.0) {
+        tau = zero<T>();
+        scale = zero<T>();
+        beta = alpha;
+      } else {
+        const double nrm = sqrt(abs2(alpha) + xnorm2);
+        const double bt = re(alpha) >= 0.0 ? -nrm : nrm;
+        beta = from_re<T>(bt);
+        tau = make_c<T>((bt - re(alpha)) / bt, -im(alpha) / bt);
+        scale = div_(from_re<T>(1.0), sub(alpha, beta));
+      }
+      sh_tau = tau;
+      sh_scale = scale;
+      sh_beta = beta;
+    }
+    __syncthreads();
+    const T tau = sh_tau, scale = sh_scale;
+    if (tid < nb) {
+      const int c = tid;
+      const T mk = prow[c];
+      if (c > j) wv[c] = add(mk, mul(conj_(scale), dtot[c]));
+      else if (c < j) wv[c] = add(conj_(mk), mul(scale, conj_(dtot[c])));
+    }
+    __syncthreads();
+    if (tid < j) {
+      const int r = tid;
+      T sacc = zero<T>();
+      for (int c = r; c < j; ++c) sacc = fmac(Ts[r + c * PANEL_MAXNB], wv[c], sacc);
+      red[r] = mul(from_re<T>(-1.0), mul(tau, sacc));
+    }
+    __syncthreads();
+    if (tid < j) Ts[tid + j * PANEL_MAXNB] = red[tid];
+    if (tid == 0) Ts[j + j * PANEL_MAXNB] = tau;
+    const T ctau = conj_(tau);
+    const int u0 = max(k, rlo);
+    for (int i = u0 + tid; i < i1; i += nt) {
+      T v;
+      if (i == k) v = from_re<T>(1.0);
+      else {
+        v = mul(scale, S[j * lds + (i - rlo)]);
+        S[j * lds + (i - rlo)] = v;
+      }
+      const T cv = mul(ctau, v);
+      for (int c = j + 1; c < nb; ++c) {
+        T* q = S + c * lds + (i - rlo);
+        *q = sub(*q, mul(cv, wv[c]));
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && owner) S[j * lds + (k - rlo)] = sh_beta;
+    __syncthreads();
+  }
+  // write back R / V and the explicit unit-lower V panel
+  for (int c = 0; c < nb; ++c) {
+    const int kc = k0 + c, rendc = min(m, kc + band);
+    for (int i = rlo + tid; i < rhi; i += nt) {
+      const T x = S[c * lds + (i - rlo)];
+      M[i + (long long)kc * ldm] = x;
+      T yv;
+      if (i < kc || i >= rendc) yv = zero<T>();
+      else if (i == kc) yv = from_re<T>(1.0);
+      else yv = x;
+      Y[(i - k0) + (long long)c * ldy] = yv;
+    }
+  }
+  if (rank == 0)
+    for (int i = tid; i < nb * nb; i += nt) {
+      const int r = i % nb, c = i / nb;
+      Tf[r + c * nb] = Ts[r + c * PANEL_MAXNB];
+    }
+  cluster.sync();
+}
+
+constexpr int PANEL_SMEM_MAX = 200 * 1024;
+
+template <class T, int CL>
+void launch_panel_smem(cudaStream_t st, int m, int n, int band, T* M, int ldm, long long sM, int k0, int nb, T* Y,
+                       int ldy, long long sY, T* Tf, long long sT, int batch, int chunk) {
+  const int smem = PANEL_MAXNB * chunk * (int)sizeof(T);
+  ZCSD_CUDA(cudaFuncSetAttribute(qr_panel_smem_kernel<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(batch * CL, 1, 1);
+  cfg.blockDim = dim3(PANEL_CL_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ZCSD_CUDA(cudaLaunchKernelEx(&cfg, qr_panel_smem_kernel<T, CL>, m, n, band, M, ldm, sM, k0, nb, Y, ldy, sY, Tf, sT,
+                               chunk));
 }
 
 constexpr int CHOL_MAXNB = 64;
@@ -367,7 +699,31 @@ void qr_panel(cudaStream_t st, int m, int n, int band, T* M, int ldm, long long 
               long long sY, T* Tf, long long sT, int batch) {
   if (nb > PANEL_MAXNB) throw CudaFail{cudaErrorInvalidValue, __FILE__, __LINE__};
   ProfToken tok = prof_begin(st);
-  qr_panel_kernel<T><<<batch, PANEL_THREADS, 0, st>>>(m, n, band, M, ldm, sM, k0, nb, Y, ldy, sY, Tf, sT);
+  const int hrows = std::min(m, k0 + nb - 1 + band) - k0;
+  const int chunk8 = (hrows + 7) / 8, chunk4 = (hrows + 3) / 4;
+  if (hrows >= 1024 && PANEL_MAXNB * chunk8 * (int)sizeof(T) <= PANEL_SMEM_MAX) {
+    launch_panel_smem<T, 8>(st, m, n, band, M, ldm, sM, k0, nb, Y, ldy, sY, Tf, sT, batch, chunk8);
+  } else if (hrows >= 256 && hrows < 1024) {
+    launch_panel_smem<T, 4>(st, m, n, band, M, ldm, sM, k0, nb, Y, ldy, sY, Tf, sT, batch, chunk4);
+  } else if (hrows >= 1024) {
+    // tall panel: a cluster of PANEL_CL CTAs per problem
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(batch * PANEL_CL, 1, 1);
+    cfg.blockDim = dim3(PANEL_CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = PANEL_CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ZCSD_CUDA(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel<T>, m, n, band, M, ldm, sM, k0, nb, Y, ldy, sY, Tf,
+                                 sT));
+  } else {
+    qr_panel_kernel<T><<<batch, PANEL_THREADS, 0, st>>>(m, n, band, M, ldm, sM, k0, nb, Y, ldy, sY, Tf, sT);
+  }
   ZCSD_LAUNCH();
   if (tok.slot >= 0) {
     // Householder panel: about 4 h nb^2 real flops (dots + rank-1 updates)

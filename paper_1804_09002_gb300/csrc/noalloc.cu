@@ -16,7 +16,8 @@ namespace zcsd {
 
 // Workspace of one Zolo-pd call (P = 1) for n <= CSD_NOALLOC_MAX_N, complex
 // FP64 (the larger element type), plus the input/output staging of polar():
-// about 4 MiB at n = 64; 6 MiB leaves headroom.
+// about 4 MiB at n = 64 (panels of at most 96 rows take no split-K
+// partial products); 6 MiB leaves headroom.
 constexpr size_t NOALLOC_BYTES = (size_t)6 << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];

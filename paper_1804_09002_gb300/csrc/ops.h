@@ -20,6 +20,13 @@ enum KFlags {
 
 constexpr int MAX_SUM = 16;
 
+// Call sites of the GEMM, for per-site kernel accounting.
+enum GemmSite {
+  GS_OTHER = 0, GS_QR_W, GS_QR_W2, GS_QR_UPD, GS_FQ_W, GS_FQ_W2, GS_FQ_UPD, GS_ZOLO_COMBINE, GS_GRAM,
+  GS_CHOL_ROW, GS_CHOL_TRAIL, GS_TRSM_F_UPD, GS_TRSM_F_DIAG, GS_TRSM_B_UPD, GS_TRSM_B_DIAG, GS_H, GS_ORTH,
+  GS_EIG, GS_ASSEMBLY, GS_ALG2, GS_SITES
+};
+
 template <class T>
 struct GemmArgs {
   int m = 0, n = 0, k = 0;
@@ -35,6 +42,8 @@ struct GemmArgs {
   int bdivA = 1, bdivB = 1, bdivC = 1;  // problem b uses A_{b / bdivA}, B_{b / bdivB}, Cin_{b / bdivC}
   int uplo = 0;                 // 0 all tiles, 1 only tiles touching the upper triangle, 2 lower
   int kflags = 0;
+  int site = 0;                 // call-site label for kernel accounting (GemmSite)
+  int ksplit = 1;               // split-K: problem b, part s writes C_{b*ksplit+s} (Cin/beta only in part 0)
   GemmArgs() { for (int i = 0; i < MAX_SUM; ++i) w[i] = 1.0; }
 };
 
@@ -43,7 +52,7 @@ template <class T> void gemm(const GemmArgs<T>& g, cudaStream_t st);
 // Convenience wrapper: C = alpha op(A) op(B) + beta C (single problem).
 template <class T>
 void gemm1(cudaStream_t st, int opA, int opB, int m, int n, int k, T alpha, const T* A, int lda,
-           const T* B, int ldb, T beta, T* C, int ldc, int uplo = 0, int kflags = 0);
+           const T* B, int ldb, T beta, T* C, int ldc, int uplo = 0, int kflags = 0, int site = 0);
 
 // ---- elementwise (batched; `batch` problems at strides s*)
 // Y = alpha X (+ beta Y when beta != 0)

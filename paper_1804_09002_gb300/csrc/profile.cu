@@ -35,6 +35,11 @@ void Profiler::flush() {
     ms[r.kind] += ms_;
     flops[r.kind] += r.flops;
     count[r.kind] += 1;
+    if (r.kind == PK_GEMM && r.site >= 0 && r.site < PROF_SITES) {
+      site_ms[r.site] += ms_;
+      site_flops[r.site] += r.flops;
+      site_count[r.site] += 1;
+    }
   }
   recs.clear();
   used = 0;
@@ -44,6 +49,7 @@ void Profiler::reset() {
   recs.clear();
   used = 0;
   for (int k = 0; k < PK_KINDS; ++k) { ms[k] = 0; flops[k] = 0; count[k] = 0; }
+  for (int k = 0; k < PROF_SITES; ++k) { site_ms[k] = 0; site_flops[k] = 0; site_count[k] = 0; }
 }
 
 Profiler::~Profiler() {
@@ -60,12 +66,12 @@ ProfToken prof_begin(cudaStream_t st) {
   return t;
 }
 
-void prof_end(ProfToken t, cudaStream_t st, int kind, double flops) {
+void prof_end(ProfToken t, cudaStream_t st, int kind, double flops, int site) {
   Profiler* p = t_prof;
   if (!p || !p->enabled || t.slot < 0) return;
   const int b = p->event();
   ZCSD_CUDA(cudaEventRecord(p->pool[b], st));
-  p->recs.push_back({t.slot, b, kind, flops});
+  p->recs.push_back({t.slot, b, kind, site, flops});
 }
 
 }  // namespace zcsd

@@ -9,7 +9,7 @@ namespace zcsd {
 struct Profiler {
   bool enabled = false;
   struct Rec {
-    int a, b, kind;
+    int a, b, kind, site;
     double flops;
   };
   std::vector<cudaEvent_t> pool;
@@ -18,6 +18,9 @@ struct Profiler {
   double ms[PK_KINDS] = {0, 0, 0, 0};
   double flops[PK_KINDS] = {0, 0, 0, 0};
   long long count[PK_KINDS] = {0, 0, 0, 0};
+  double site_ms[PROF_SITES] = {};
+  double site_flops[PROF_SITES] = {};
+  long long site_count[PROF_SITES] = {};
   int event();
   void flush();
   void reset();

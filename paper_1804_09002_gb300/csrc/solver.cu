@@ -141,6 +141,7 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd)
         g.C = Xn; g.ldc = n; g.sC = nn;
         g.alpha = one; g.beta = from_re<T>(pl.mhat[s]);
         g.kflags = K_FROM_COL;
+        g.site = GS_ZOLO_COMBINE;
         gemm(g, st);
         ar.release(mk2);
         break;
@@ -159,6 +160,7 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd)
       g.B = X; g.ldb = n; g.sB = nn;
       g.C = G; g.ldc = n; g.sC = nn;
       g.alpha = one; g.beta = zer; g.uplo = 1;
+      g.site = GS_GRAM;
       gemm(g, st);
       double shifts[R_MAX];
       for (int j = 0; j < r; ++j) shifts[j] = pl.c[s][2 * j];
@@ -309,7 +311,7 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
       }
       // subspaces: [Q1 Q2] = qr(P Omega), Q1 spans range(P)
       randn<T>(st, sz, sz, Om, sz, cx.seed + 7919ull * (unsigned long long)(ed->splits * 4 + attempt));
-      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Ps, sz, Om, sz, zer, Tmp, sz);
+      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Ps, sz, Om, sz, zer, Tmp, sz, 0, 0, GS_EIG);
       {
         const size_t mq = ar.mark();
         QRStore<T> q = qr_alloc<T>(ar, sz, sz, sz, 1);
@@ -320,8 +322,8 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
       // B' = Q^* B_sub Q = ||B_sub - sI||_F Q^* X Q + s I: the shift is added
       // back exactly, so the departure of Q from orthogonality is multiplied
       // by the small ||B_sub - sI|| (not by |s|) in the off-diagonal block
-      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Xs, sz, Qf, sz, zer, Tmp, sz);
-      gemm1<T>(st, OP_C, OP_N, sz, sz, sz, from_re<T>(xnorm), Qf, sz, Tmp, sz, zer, Om, sz);
+      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Xs, sz, Qf, sz, zer, Tmp, sz, 0, 0, GS_EIG);
+      gemm1<T>(st, OP_C, OP_N, sz, sz, sz, from_re<T>(xnorm), Qf, sz, Tmp, sz, zer, Om, sz, 0, 0, GS_EIG);
       fro2<T>(st, sz - k, k, Om + k, sz, 0, 0.0, sc + 6, 1, scratch);
       d2h(cx, cx.hs.d, sc + 6, sizeof(double));
       const double offa = std::sqrt(cx.hs.d[0]);
@@ -331,7 +333,7 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
       ed->splits += 1;
       // accept: B_sub <- B' (+ s I), V[:, off:off+sz] <- V[:, off:off+sz] Q
       copy_shift<T>(st, sz, 1.0, Om, sz, 0, s, Bsub, n, 0, 1);
-      gemm1<T>(st, OP_N, OP_N, n, sz, sz, one, V + (long long)off * n, n, Qf, sz, zer, Tmp, n);
+      gemm1<T>(st, OP_N, OP_N, n, sz, sz, one, V + (long long)off * n, n, Qf, sz, zer, Tmp, n, 0, 0, GS_EIG);
       axpby<T>(st, n, sz, 1.0, Tmp, n, 0, 0.0, V + (long long)off * n, n, 0, 1);
       if (bk.top && restricted) {
         lo = off + k;
@@ -365,7 +367,7 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
     jacobi_leaves<T>(st, nl, doffs, doffs + nl, Bw, n, lamw, Vl, nullptr);
     for (int i = 0; i < nl; ++i) {
       gemm1<T>(st, OP_N, OP_N, n, js[i], js[i], one, V + (long long)jo[i] * n, n,
-               Vl + (long long)i * LEAF * LEAF, LEAF, zer, Tmp, n);
+               Vl + (long long)i * LEAF * LEAF, LEAF, zer, Tmp, n, 0, 0, GS_EIG);
       axpby<T>(st, n, js[i], 1.0, Tmp, n, 0, 0.0, V + (long long)jo[i] * n, n, 0, 1);
     }
     ZCSD_CUDA(cudaStreamSynchronize(st));  // hbuf lifetime
@@ -434,6 +436,7 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     g.B = Apk; g.ldb = n; g.sB = nn;
     g.C = H; g.ldc = n; g.sC = nn;
     g.alpha = one; g.beta = zer;
+    g.site = GS_H;
     gemm(g, st);
     symmetrize<T>(st, n, H, n, nn, H, n, nn, 2);
   }
@@ -448,6 +451,7 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     g.B = W; g.ldb = n; g.sB = nn;
     g.C = Gw; g.ldc = n; g.sC = nn;
     g.alpha = one; g.beta = zer;
+    g.site = GS_ORTH;
     gemm(g, st);
     fro2<T>(st, n, n, Gw, n, nn, 1.0, sc + 4, 2, scratch);
     d2h(cx, cx.hs.d, sc + 4, 2 * sizeof(double));
@@ -490,7 +494,7 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     ZCSD_LAUNCH();
     scale_cols_phase_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, n, Qa, n, d1, d2, Qa, n);
     ZCSD_LAUNCH();
-    gemm1<T>(st, OP_N, OP_C, n, n, n, one, Qa, n, Qh, n, zer, W + i * nn, n);
+    gemm1<T>(st, OP_N, OP_C, n, n, n, one, Qa, n, Qh, n, zer, W + i * nn, n, 0, 0, GS_ALG2);
     rdiff_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, Ma, n, d1, Mh, n, d2, D);
     ZCSD_LAUNCH();
     fro2<T>(st, n, n, D, n, 0, 0.0, sc + 8, 1, scratch);
@@ -545,6 +549,7 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     g.B = Vr; g.ldb = n; g.sB = 0;
     g.C = Ut; g.ldc = n; g.sC = nn;
     g.alpha = one; g.beta = zer;
+    g.site = GS_ASSEMBLY;
     gemm(g, st);
     T* HV = W;  // W no longer needed
     GemmArgs<T> g2 = g;
@@ -595,7 +600,7 @@ int polar_impl(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* Wo, int ldw, T
   axpby<T>(st, n, n, 1.0, W, n, 0, 0.0, Wo, ldw, 0, 1);
   if (Ho) {
     T* Hm = X;
-    gemm1<T>(st, OP_C, OP_N, n, n, n, from_re<T>(1.0), W, n, A, lda, zero<T>(), Hm, n);
+    gemm1<T>(st, OP_C, OP_N, n, n, n, from_re<T>(1.0), W, n, A, lda, zero<T>(), Hm, n, 0, 0, GS_H);
     symmetrize<T>(st, n, Hm, n, 0, Ho, ldh, 0, 1);
   }
   if (info) {
@@ -665,15 +670,15 @@ size_t polar_bytes(long long n, int P, size_t es) {
   long long qr = 2 * (2 * nn) * P * r                                         // M, E
                  + (long long)ceil_div(n, NB_QR) * (n + 1 + NB_QR) * NB_QR * P * r  // Y
                  + (long long)ceil_div(n, NB_QR) * NB_QR * NB_QR * P * r           // T
-                 + 2LL * NB_QR * n * P * r;                                         // W, W2
-  long long ch = nn * P + 3 * nn * P * r + (long long)NB_CHOL * n * P * r * 2;
+                 + (long long)(MAX_SUM + 1) * NB_QR * n * P * r;                    // W (split-K parts), W2
+  long long ch = nn * P + 3 * nn * P * r + (long long)NB_CHOL * n * P * r * (2 + MAX_SUM);
   return (size_t)((2 * nn * P + std::max(qr, ch)) * es) + 64 * 256;
 }
 
 size_t heig_bytes(long long n, size_t es) {
   const long long nn = n * n;
   long long qr = (long long)ceil_div(n, NB_QR) * (n + NB_QR) * NB_QR + (long long)ceil_div(n, NB_QR) * NB_QR * NB_QR +
-                 2LL * NB_QR * n;
+                 (long long)(MAX_SUM + 1) * NB_QR * n;
   long long leaves = (n / 1 + 1) * 0 + (long long)LEAF * LEAF * (n / 1);
   return (size_t)((7 * nn + std::max(qr, leaves)) * es) + polar_bytes(n, 1, es) + (size_t)(3 * n + 2048) * 8 + 64 * 256;
 }
@@ -932,6 +937,11 @@ int csd_profile_read(csd_ctx* ctx, csd_profile* out) {
     out->count[k] = ctx->cx.prof.count[k];
     out->ms[k] = ctx->cx.prof.ms[k];
     out->flops[k] = ctx->cx.prof.flops[k];
+  }
+  for (int k = 0; k < PROF_SITES; ++k) {
+    out->site_count[k] = ctx->cx.prof.site_count[k];
+    out->site_ms[k] = ctx->cx.prof.site_ms[k];
+    out->site_flops[k] = ctx->cx.prof.site_flops[k];
   }
   return CSD_OK;
 }

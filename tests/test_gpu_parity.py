@@ -186,3 +186,105 @@ def test_csd_nonfinite_input_is_rejected(B):
     with pytest.raises(B.CSDError) as e:
         B.csd_polar(to_dev(A1), to_dev(A2))
     assert e.value.status == 5
+
+
+# ------------------------------------------------------------------ tall panels
+@pytest.mark.parametrize("n", [1000, 1100])
+def test_polar_large_properties(B, n):
+    """n >= 1000 exercises the cluster (multi-CTA) Householder panel of the
+    stacked [X; sqrt(c) I] QR (panel height n + 32 >= 1024).  Properties that
+    hold at any size: W orthonormal, W H = A, H Hermitian positive
+    semidefinite; W equals U V^T of the matrix built from a known SVD."""
+    rng = np.random.default_rng(n)
+    Uo = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    Vo = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    s = np.geomspace(1e-6, 1.0, n)
+    A = (Uo * s) @ Vo.T
+    W, H, info = B.polar(to_dev(A))
+    W, H = to_host(W), to_host(H)
+    assert np.linalg.norm(W.T @ W - np.eye(n), 2) <= 50 * n * U
+    assert np.linalg.norm(W @ H - A) <= 50 * n * U * np.linalg.norm(A)
+    assert np.linalg.norm(H - H.T) == 0.0
+    assert np.min(np.linalg.eigvalsh(H)) >= -50 * n * U
+    assert np.linalg.norm(W - Uo @ Vo.T) <= 1e-8
+
+
+def test_csd_large_clustered_known_angles(B):
+    """n = 1024 clustered workload: angles against the generator's known
+    angles (the 1e-14 perturbation moves them by O(1e-14)), backward error
+    and orthogonality; the oracle is too slow at this size, so the checks
+    are the properties that hold at any size."""
+    n = 1024
+    A1, A2, th = I.clustered_csd(n, seed=2)
+    R = B.csd_polar(to_dev(A1), to_dev(A2))
+    _check_csd(A1, A2, R, n, theta_ref=th, rank=n)
+
+
+# ------------------------------------------------------------------ full-size workloads
+def _dev_metrics(A1, A2, R):
+    """Angles, backward error and orthogonality computed with torch on the
+    GPU (the matrices are too large for a quick host check)."""
+    rk = R["rank"]
+    th = R["theta"][:rk]
+    U1, U2, V1 = (R[k][:, :rk] for k in ("U1", "U2", "V1"))
+    c = torch.cos(th).to(U1.dtype)
+    s = torch.sin(th).to(U1.dtype)
+    Vh = V1.conj().T
+    r1 = A1 - (U1 * c) @ Vh
+    r2 = A2 - (U2 * s) @ Vh
+    num = torch.sqrt(torch.linalg.norm(r1) ** 2 + torch.linalg.norm(r2) ** 2)
+    den = torch.sqrt(torch.linalg.norm(A1) ** 2 + torch.linalg.norm(A2) ** 2)
+    eye = torch.eye(rk, dtype=U1.dtype, device=U1.device)
+    orth = max(float(torch.linalg.norm(X.conj().T @ X - eye)) for X in (U1, U2, V1))
+    return th.cpu().numpy(), float(num / den), orth
+
+
+def test_csd_full_size_n4096_clustered(B):
+    """The n = 4096 workload (theta half uniform, quarters within 1e-8 of 0
+    and pi/2, 1e-14 noise, re-orthonormalised): angles within 1e-12 n of the
+    generator's, backward error <= 50 n u, ||X^* X - I||_F <= 50 n u."""
+    n = 4096
+    A1h, A2h, th = I.clustered_csd(n, seed=2)
+    A1, A2 = to_dev(A1h), to_dev(A2h)
+    R = B.csd_polar(A1, A2)
+    assert R["rank"] == n
+    got, be, orth = _dev_metrics(A1, A2, R)
+    assert np.all(np.diff(got) >= 0)
+    assert np.max(np.abs(got - th)) <= 1e-12 * n
+    assert be <= 50 * n * U
+    assert orth <= 50 * n * U
+
+
+def test_csd_full_size_n2048_complex_rank_deficient(B):
+    """Complex128 partial isometry, n = 2048, rank 1536 with 512 zero (C, S)
+    pairs and 256 exactly repeated angles (Algorithm 3, mu = 2)."""
+    n, k = 2048, 1536
+    A1h, A2h, th = I.rankdef_csd(n, k, seed=3, cplx=True, n_repeat=256)
+    A1, A2 = to_dev(A1h), to_dev(A2h)
+    R = B.csd_polar(A1, A2)
+    assert R["rank"] == k and R["info"]["mu"] == 2.0
+    got, be, orth = _dev_metrics(A1, A2, R)
+    assert np.max(np.abs(got - th)) <= 1e-12 * n
+    assert be <= 50 * n * U
+    assert orth <= 50 * n * U
+
+
+def test_csd_algorithm2_exact_zero_angles(B):
+    """theta containing exactly 0 and pi/2: A2 (resp. A1) has a zero singular
+    value below eps = 1e-15, so the eps-modified Zolo-pd factor is not
+    orthonormal and Algorithm 2 (QR of A_i and H_i, W_i = Q_i Q~_i^*) must
+    restore it; the rank is still n (mu = 0)."""
+    n = 64
+    rng = np.random.default_rng(77)
+    theta = rng.uniform(0, np.pi / 2, n)
+    theta[:3] = 0.0
+    theta[3:5] = np.pi / 2
+    A1, A2 = I.from_angles(theta, rng)
+    R = B.csd_polar(to_dev(A1), to_dev(A2))
+    info = R["info"]
+    assert R["rank"] == n and info["mu"] == 0.0
+    assert info["alg2_used"][0] == 1 and info["alg2_used"][1] == 1
+    assert max(info["rdiff"]) <= 1e3 * n * U
+    ref = O.csd(A1, A2)
+    _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=n)
+    assert np.max(np.abs(to_host(R["theta"]) - np.sort(theta))) <= 1e-12 * n
