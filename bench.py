@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-n", type=int, default=512, help="oracle sample size for the CPU baseline")
+    ap.add_argument("--tc", type=int, default=0, help="1: real FP64 products on the tcgen05 tensor cores (sliced BF16)")
     return ap.parse_args()
 
 
@@ -187,6 +188,7 @@ def main():
     colmaj = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).to(dev).t()
     A1, A2 = colmaj(A1h), colmaj(A2h)
     ctx = B.Context(local)
+    ctx.set_tensor_cores(bool(args.tc))
     out = {k: torch.empty((n, n), dtype=torch.float64, device=dev).t() for k in ("U1", "U2", "V1")}
     out["theta"] = torch.empty(n, dtype=torch.float64, device=dev)
 
@@ -250,9 +252,9 @@ def main():
         e2e = {"value": te, "unit": "s/CSD", "h2d_bytes_per_step": 2 * n * n * 8,
                "d2h_bytes_per_step": 3 * n * n * 8 + n * 8}
     # ---- roofline of the dominant kernel (GEMM on the FP64 FMA pipe)
-    kinds = ["gemm", "qr_panel", "potrf", "jacobi"]
+    kinds = ["gemm", "qr_panel", "potrf", "jacobi", "tc_gemm"]
     kms = {k: prof.ms[i] for i, k in enumerate(kinds)}
-    dom = max(range(4), key=lambda i: prof.ms[i])
+    dom = max(range(5), key=lambda i: prof.ms[i])
     avg_ms = prof.ms[dom] / max(prof.count[dom], 1)
     flops_per_launch = prof.flops[dom] / max(prof.count[dom], 1)
     peak = fp64_alu_peak_tflops()

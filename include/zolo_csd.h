@@ -43,6 +43,7 @@ extern "C" {
 #define CSD_ERR_ALLOC 6           /* device workspace allocation failed */
 #define CSD_ERR_INTERNAL 7        /* internal consistency check failed */
 #define CSD_ERR_NO_DEVICE 8       /* no usable CUDA device for the context */
+#define CSD_ERR_DEVICE_TIMEOUT 9  /* a bounded wait inside a tensor-core kernel gave up */
 
 #define CSD_F64 0
 #define CSD_C128 1
@@ -149,16 +150,17 @@ int zolo_plan(double ell0, int rmax, int max_iter, int* r_out, double* ell_out);
 
 /* Kernel accounting, for roofline reports (not needed for computing).
  * Kinds: 0 = GEMM (FP64 FMA tiles), 1 = Householder QR panel, 2 = Cholesky
- * diagonal block, 3 = Jacobi leaves.  While enabled, each launch of these
+ * diagonal block, 3 = Jacobi leaves, 4 = tensor-core FP64 GEMM (sliced BF16
+ * products on tcgen05; `flops` counts the FP64-equivalent 2mnk).  While enabled, each launch of these
  * kernels is bracketed by CUDA events on the context stream; `flops` sums
  * the multiply-add work each launch executes (2 per real FMA, 8 per complex
  * FMA; QR panel and Cholesky block use their textbook counts).
  * csd_profile_enable resets the counters; csd_profile_read synchronises the
  * stream and returns the totals since then. */
 typedef struct {
-  long long count[4];
-  double ms[4];
-  double flops[4];
+  long long count[5];
+  double ms[5];
+  double flops[5];
   /* GEMM launches split by call site (0 other, 1-3 QR panel update, 4-6 Q
    * formation, 7 Zolotarev term sum, 8 Gram matrix, 9-10 Cholesky, 11-14
    * triangular solves, 15 H, 16 orthogonality check, 17 Zolo-eig,
@@ -169,6 +171,20 @@ typedef struct {
 } csd_profile;
 
 int csd_profile_enable(csd_ctx* ctx, int enable);
+
+/* Run the real FP64 matrix products of this context on the tcgen05 tensor
+ * cores instead of the FP64 FMA pipe.  enable = 0 (the default) keeps every
+ * product on the FP64 pipe; otherwise bit s of `enable` selects the products
+ * of call site s (the site numbering of csd_profile).  enable = -1 selects
+ * every site except 3 (the trailing update of the stacked QR factorization,
+ * whose result needs componentwise FP64 accuracy; sliced products are
+ * accurate relative to the row and column maxima of the operands).
+ * The products stay FP64-accurate: each operand is split exactly into seven
+ * BF16 slices with per-row / per-column power-of-two scaling, the slice
+ * products are accumulated in FP32 where that is exact and in FP64 otherwise
+ * (error of the same order as an FP64 product).  Complex data always uses
+ * the FP64 pipe.  Returns 0 or -1 (NULL context). */
+int csd_set_tensor_cores(csd_ctx* ctx, int enable);
 int csd_profile_read(csd_ctx* ctx, csd_profile* out);
 
 /* Process-wide number of kernels this library has launched so far. */

@@ -52,7 +52,7 @@ class csd_info(ctypes.Structure):
 
 
 class csd_profile(ctypes.Structure):
-    _fields_ = [("count", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4), ("flops", ctypes.c_double * 4),
+    _fields_ = [("count", ctypes.c_longlong * 5), ("ms", ctypes.c_double * 5), ("flops", ctypes.c_double * 5),
                 ("site_count", ctypes.c_longlong * 24), ("site_ms", ctypes.c_double * 24),
                 ("site_flops", ctypes.c_double * 24)]
 
@@ -79,13 +79,14 @@ def _load():
     lib.zolo_coeffs.argtypes = [cd, ci, vp, vp, ctypes.POINTER(cd), ctypes.POINTER(cd)]
     lib.zolo_plan.argtypes = [cd, ci, ci, vp, vp]
     lib.csd_profile_enable.argtypes = [vp, ci]
+    lib.csd_set_tensor_cores.argtypes = [vp, ci]
     lib.csd_profile_read.argtypes = [vp, ctypes.POINTER(csd_profile)]
     lib.csd_launch_count.argtypes = []
     lib.csd_launch_count.restype = ctypes.c_longlong
     lib.csd_status_str.argtypes = [ci]
     lib.csd_status_str.restype = ctypes.c_char_p
     for f in ("csd_create", "csd_set_stream", "csd_destroy", "csd_polar", "polar", "heig", "zolo_coeffs",
-              "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc"):
+              "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc", "csd_set_tensor_cores"):
         getattr(lib, f).restype = ci
     return lib
 
@@ -94,7 +95,7 @@ lib = _load()
 
 EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes", "csd_polar", "polar", "heig",
             "zolo_coeffs", "zolo_plan", "csd_status_str", "csd_profile_enable", "csd_profile_read",
-            "csd_launch_count", "polar_noalloc"]
+            "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores"]
 
 
 class CSDError(RuntimeError):
@@ -216,6 +217,14 @@ class Context:
             lib.csd_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream))
         else:
             lib.csd_set_stream(self._h, None)
+
+    def set_tensor_cores(self, enable=True, sites=-1):
+        """Run real FP64 products on the tcgen05 tensor cores (sliced BF16,
+        FP64-accurate) instead of the FP64 FMA pipe; `sites` is a bit mask
+        over the GEMM call sites (csd_profile.SITES), -1 = all."""
+        st = lib.csd_set_tensor_cores(self._h, (sites if sites else 0) if enable else 0)
+        if st != 0:
+            raise CSDError(st, "csd_set_tensor_cores")
 
     def workspace_bytes(self):
         return lib.csd_workspace_bytes(self._h)

@@ -7,7 +7,10 @@
 // needs one shared-memory load per two FMAs, and relies on several resident
 // CTAs per SM to cover global-load latency.  Grids are sized by the output
 // tiles of all problems of a batch together.
+#include <type_traits>
+
 #include "ops.h"
+#include "tc_gemm.h"
 
 namespace zcsd {
 
@@ -170,6 +173,12 @@ double gemm_flops(const GemmArgs<T>& g, int BM, int BN) {
 template <class T>
 void gemm(const GemmArgs<T>& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return;
+  if constexpr (std::is_same<T, double>::value) {
+    if (tc_will_handle(g)) {
+      tc_gemm(g, st, *t_tc.ar, t_tc.err);
+      return;
+    }
+  }
   const bool narrow = g.m <= 32;
   ProfToken tok = prof_begin(st);
   if (narrow) gemm_dispatch<T, 32>(g, st);

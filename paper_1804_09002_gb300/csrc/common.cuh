@@ -85,7 +85,7 @@ void count_launch();
 // Optional per-kind kernel timing (CUDA events on the launch stream), used
 // for roofline reports.  prof_begin/prof_end bracket one launch; both are
 // no-ops unless a profiler is active on the calling thread.
-enum ProfKind { PK_GEMM = 0, PK_QR_PANEL = 1, PK_POTRF = 2, PK_JACOBI = 3, PK_KINDS = 4 };
+enum ProfKind { PK_GEMM = 0, PK_QR_PANEL = 1, PK_POTRF = 2, PK_JACOBI = 3, PK_TC = 4, PK_KINDS = 5 };
 struct ProfToken {
   int slot = -1;
 };

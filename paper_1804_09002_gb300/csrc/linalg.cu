@@ -1,6 +1,9 @@
 // Blocked Householder QR (compact WY), blocked Cholesky and the paired
 // triangular solves, as sequences of panel kernels and batched GEMMs.
+#include <type_traits>
+
 #include "linalg.h"
+#include "tc_gemm.h"
 
 namespace zcsd {
 
@@ -24,6 +27,20 @@ static int pick_ksplit(int m, int n, int k, int batch, int bm, int kmin = 256) {
     }
   }
   return best;
+}
+
+// Products the tensor-core path takes run unsplit (it takes the whole K range).
+template <class T>
+static int resolve_ksplit(GemmArgs<T>& g, int ks) {
+  g.ksplit = ks;
+  if constexpr (std::is_same<T, double>::value) {
+    if (ks > 1) {
+      GemmArgs<T> probe = g;
+      probe.ksplit = 1;
+      if (tc_will_handle(probe)) g.ksplit = 1;
+    }
+  }
+  return g.ksplit;
 }
 
 template <class T>
@@ -59,15 +76,14 @@ void qr_factor(cudaStream_t st, Arena& ar, QRStore<T>& q, T* M, int ldm, long lo
     const int nc = n - (k0 + nb);
     if (nc <= 0) continue;
     // W = Y^* C, split along K into ks partial products W_s
-    const int ks = pick_ksplit(nb, nc, h, q.batch, 32);
     GemmArgs<T> g;
     g.batch = q.batch;
-    g.ksplit = ks;
     g.m = nb; g.n = nc; g.k = h; g.opA = OP_C; g.opB = OP_N;
     g.A = Yp; g.lda = q.ldy; g.sA = q.sY;
     g.B = M + k0 + (long long)(k0 + nb) * ldm; g.ldb = ldm; g.sB = sM;
     g.C = W; g.ldc = NB_QR; g.sC = sW;
     g.site = GS_QR_W;
+    const int ks = resolve_ksplit(g, pick_ksplit(nb, nc, h, q.batch, 32));
     g.alpha = one; g.beta = zer;
     gemm(g, st);
     // W2 = T^* sum_s W_s   (T upper triangular: op(A)[i,k] = conj(T[k,i]) = 0 for k > i)
@@ -115,15 +131,14 @@ void qr_form_q(cudaStream_t st, Arena& ar, const QRStore<T>& q, T* E, int lde, l
     const T* Yp = q.Y + (long long)p * q.ldy * NB_QR;
     const T* Tp = q.Tf + (long long)p * NB_QR * NB_QR;
     T* Es = E + k0 + (long long)k0 * lde;
-    const int ks = pick_ksplit(nb, nc, h, q.batch, 32);
     GemmArgs<T> g;  // W = Y^* E_sub, split along K
     g.batch = q.batch;
-    g.ksplit = ks;
     g.m = nb; g.n = nc; g.k = h; g.opA = OP_C; g.opB = OP_N;
     g.A = Yp; g.lda = q.ldy; g.sA = q.sY;
     g.B = Es; g.ldb = lde; g.sB = sE;
     g.C = W; g.ldc = NB_QR; g.sC = sW;
     g.site = GS_FQ_W;
+    const int ks = resolve_ksplit(g, pick_ksplit(nb, nc, h, q.batch, 32));
     g.alpha = one; g.beta = zer;
     gemm(g, st);
     GemmArgs<T> g2;  // W2 = T sum_s W_s
@@ -198,10 +213,8 @@ void trsm_pair(cudaStream_t st, Arena& ar, int n, const T* X, int ldx, long long
   for (int k0 = 0; k0 < n; k0 += NB_CHOL) {
     const int nb = std::min(NB_CHOL, n - k0);
     // Tmp_s = [s == 0] X[:, k] - Yt[:, K_s] R[K_s, k] over K chunks K_s of [0, k0)
-    const int ks = k0 > 0 ? pick_ksplit(n, nb, k0, batch, 64) : 1;
     GemmArgs<T> g;
     g.batch = batch;
-    g.ksplit = ks;
     g.m = n; g.n = nb; g.k = k0; g.opA = OP_N; g.opB = OP_N;
     g.A = Yt; g.lda = ldt; g.sA = sT;
     g.B = Z + (long long)k0 * ldz; g.ldb = ldz; g.sB = sZ;
@@ -210,6 +223,7 @@ void trsm_pair(cudaStream_t st, Arena& ar, int n, const T* X, int ldx, long long
     g.site = GS_TRSM_F_UPD;
     g.alpha = mone; g.beta = one;
     if (k0 == 0) { g.k = 0; g.nsum = 0; }
+    const int ks = resolve_ksplit(g, k0 > 0 ? pick_ksplit(n, nb, k0, batch, 64) : 1);
     gemm(g, st);
     // Yt[:, k] = (sum_s Tmp_s) R_kk^{-1}
     GemmArgs<T> g2;
@@ -229,10 +243,8 @@ void trsm_pair(cudaStream_t st, Arena& ar, int n, const T* X, int ldx, long long
     const int k0 = bk * NB_CHOL;
     const int nb = std::min(NB_CHOL, n - k0);
     const int ke = k0 + nb;
-    const int ks = ke < n ? pick_ksplit(n, nb, n - ke, batch, 64) : 1;
     GemmArgs<T> g;
     g.batch = batch;
-    g.ksplit = ks;
     g.m = n; g.n = nb; g.k = n - ke; g.opA = OP_N; g.opB = OP_C;
     g.A = Tt + (long long)ke * ldt; g.lda = ldt; g.sA = sT;
     g.B = Z + k0 + (long long)ke * ldz; g.ldb = ldz; g.sB = sZ;
@@ -241,6 +253,7 @@ void trsm_pair(cudaStream_t st, Arena& ar, int n, const T* X, int ldx, long long
     g.site = GS_TRSM_B_UPD;
     g.alpha = mone; g.beta = one;
     if (ke >= n) { g.k = 0; g.nsum = 0; }
+    const int ks = resolve_ksplit(g, ke < n ? pick_ksplit(n, nb, n - ke, batch, 64) : 1);
     gemm(g, st);
     GemmArgs<T> g2;
     g2.batch = batch;

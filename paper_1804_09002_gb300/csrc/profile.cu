@@ -35,7 +35,7 @@ void Profiler::flush() {
     ms[r.kind] += ms_;
     flops[r.kind] += r.flops;
     count[r.kind] += 1;
-    if (r.kind == PK_GEMM && r.site >= 0 && r.site < PROF_SITES) {
+    if ((r.kind == PK_GEMM || r.kind == PK_TC) && r.site >= 0 && r.site < PROF_SITES) {
       site_ms[r.site] += ms_;
       site_flops[r.site] += r.flops;
       site_count[r.site] += 1;

@@ -15,9 +15,9 @@ struct Profiler {
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> recs;
   int used = 0;
-  double ms[PK_KINDS] = {0, 0, 0, 0};
-  double flops[PK_KINDS] = {0, 0, 0, 0};
-  long long count[PK_KINDS] = {0, 0, 0, 0};
+  double ms[PK_KINDS] = {};
+  double flops[PK_KINDS] = {};
+  long long count[PK_KINDS] = {};
   double site_ms[PROF_SITES] = {};
   double site_flops[PROF_SITES] = {};
   long long site_count[PROF_SITES] = {};

@@ -8,6 +8,7 @@
 
 #include "../../include/zolo_csd.h"
 #include "solver.h"
+#include "tc_gemm.h"
 
 namespace zcsd {
 
@@ -261,8 +262,12 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
     // split is accepted when ||B'_21||_F <= off_tol.  Both are measured
     // against ||B||_F of the whole matrix, which is what the backward error
     // of the eigendecomposition is relative to.
+    // ||B'_21||_F is a backward perturbation of B; with at most ~log2(n / 64)
+    // levels of splits, 2 n u ||B||_F per split keeps the eigendecomposition's
+    // share of the CSD backward error (Theorem 3.1, term Delta B_2) near
+    // 12 n u, inside the 50 n u bound; small blocks keep 50 sqrt(sz) u ||B||_F.
     const double scal_tol = 100.0 * U_ROUND * bnorm * std::sqrt((double)sz);
-    const double off_tol = 50.0 * U_ROUND * bnorm * std::sqrt((double)sz);
+    const double off_tol = std::max(50.0 * std::sqrt((double)sz), 2.0 * n) * U_ROUND * bnorm;
     const double s0 = s;
     double spread = 0.0;  // ||B_sub - s0 I||_F / sqrt(sz): RMS distance of the eigenvalues from s0
     for (int attempt = 0; attempt < 7 && !done; ++attempt) {
@@ -719,6 +724,11 @@ int run_with_ws(Ctx& cx, size_t need, csd_info* info, F body) {
     explicit ProfScope(Profiler* p) : prev(t_prof) { t_prof = p; }
     ~ProfScope() { t_prof = prev; }
   } scope(&cx.prof);
+  struct TcScope {  // tensor-core dispatch state for this call
+    TcState prev;
+    TcScope() : prev(t_tc) {}
+    ~TcScope() { t_tc = prev; }
+  } tc_scope;
   for (int attempt = 0; attempt < 4; ++attempt) {
     status = ensure_ws(cx, need);
     if (status) break;
@@ -726,7 +736,22 @@ int run_with_ws(Ctx& cx, size_t need, csd_info* info, F body) {
     ar.base = cx.ws;
     ar.cap = cx.ws_bytes;
     try {
+      int* tc_err = nullptr;
+      if (cx.tensor_cores) {
+        tc_err = ar.get<int>(1);
+        ZCSD_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int), cx.stream));
+      }
+      t_tc.enabled = cx.tensor_cores;
+      t_tc.sites = cx.tc_sites;
+      t_tc.ar = &ar;
+      t_tc.err = tc_err;
       status = body(ar);
+      if (tc_err) {
+        int h = 0;
+        ZCSD_CUDA(cudaMemcpyAsync(&h, tc_err, sizeof(int), cudaMemcpyDeviceToHost, cx.stream));
+        ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+        if (h && (status == CSD_OK || status == CSD_WARN_ALG2_RCHECK)) status = CSD_ERR_DEVICE_TIMEOUT;
+      }
       break;
     } catch (ArenaOverflow& o) {
       cudaStreamSynchronize(cx.stream);
@@ -911,6 +936,17 @@ long long csd_workspace_bytes(const csd_ctx* ctx) { return ctx ? (long long)ctx-
 
 long long csd_launch_count(void) { return launch_count(); }
 
+int csd_set_tensor_cores(csd_ctx* ctx, int enable) {
+  if (!ctx) return -1;
+  ctx->cx.tensor_cores = enable != 0;
+  // -1: every site whose products stay FP64-accurate when sliced.  The
+  // trailing update C -= Y W2 of the stacked [X; sqrt(c) I] factorization is
+  // excluded: it needs the componentwise accuracy of the FP64 pipe (sliced
+  // products are accurate relative to row / column maxima only).
+  ctx->cx.tc_sites = enable == -1 ? ~(1u << GS_QR_UPD) : (unsigned)enable;
+  return CSD_OK;
+}
+
 int csd_profile_enable(csd_ctx* ctx, int enable) {
   if (!ctx) return -1;
   try {
@@ -1009,6 +1045,7 @@ const char* csd_status_str(int s) {
     case CSD_ERR_ALLOC: return "device workspace allocation failed";
     case CSD_ERR_INTERNAL: return "internal error";
     case CSD_ERR_NO_DEVICE: return "no CUDA device";
+    case CSD_ERR_DEVICE_TIMEOUT: return "a tensor-core wait on the device timed out";
     default: return "unknown status";
   }
 }

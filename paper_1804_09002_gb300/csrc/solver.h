@@ -28,6 +28,8 @@ struct Ctx {
   bool plan_ready = false;
   unsigned long long seed = 0x5EEDull;
   Profiler prof;
+  bool tensor_cores = false;
+  unsigned tc_sites = 0;
 };
 
 struct PolarDiag {

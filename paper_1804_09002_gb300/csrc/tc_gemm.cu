@@ -1,0 +1,400 @@
+// FP64-accurate GEMM on the tcgen05 tensor cores (sm_103a) by error-free
+// operand slicing (the Ozaki scheme: Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59, 2012).
+//
+// Every row i of op(A) is scaled by 2^-ea_i (ea_i = exponent of the row's
+// largest |entry|, shared by all terms of a grouped sum) and expanded as
+// 2^-8 sum_{s=1..7} qa_s 2^-8(s-1) with integers |qa_s| <= 256; likewise every
+// column j of op(B) with eb_j.  Each slice q~_s = q_s 2^-8(s-1) is exact in
+// BF16.  Then
+//   op(A) op(B) = 2^(ea_i + eb_j - 16) sum_{s+t <= 8} A~_s B~_t  (+ O(2^-56) x row/col maxima),
+// and every BF16 x BF16 product is exact in FP32.  The 28 slice products are
+// issued as tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM) into six
+// accumulators by g = s + t: g = 2, 3, 4, 5, 6 and "g >= 7".  For g <= 6 the
+// integer sums of 128 consecutive k stay below 2^24 (|q_1| <= 256, |q_s| <=
+// 128 for s >= 2), so those accumulators are exact and are added into FP64
+// registers every 128 k.  The g >= 7 accumulator holds terms below 2^-40 of
+// the result; its FP32 rounding is far below FP64 rounding, and it is added
+// at the end.  The FP64 sum is then scaled by 2^(ea_i + eb_j - 16).
+//
+// Layout: a CTA computes a 128 x 64 FP64 output tile with 128 threads and
+// 6 x 64 TMEM columns (512 allocated).  Per
+// 64-wide k chunk it stages 7 A slices (128 x 64) and 7 B slices (64 x 64) in
+// shared memory as K-major 8 x 16-byte core matrices (no swizzle), thread 0
+// issues the 28 x 4 MMAs (M = 128, N = 64, K = 16), completion is signalled
+// through tcgen05.commit on an mbarrier (bounded wait), and the four warps
+// read their 32 TMEM lanes each with tcgen05.ld.
+#include <cuda_bf16.h>
+
+#include "tc_gemm.h"
+
+namespace zcsd {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 64, TC_S = 7;
+constexpr int TC_THREADS = 128;
+constexpr int TC_NACC = 6;          // accumulators: g = 2..6 exact, g >= 7
+constexpr int TC_TMEM_COLS = 512;   // power of two >= TC_NACC * TC_BN
+constexpr int TC_SLICE_A_BYTES = TC_BM * TC_BK * 2;  // 16 KiB
+constexpr int TC_SLICE_B_BYTES = TC_BN * TC_BK * 2;  // 8 KiB
+constexpr int TC_SMEM = TC_S * (TC_SLICE_A_BYTES + TC_SLICE_B_BYTES) + 1024;
+constexpr long long TC_WAIT_LIMIT = 1LL << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: start address, leading-dimension
+// byte offset (next core matrix along K), stride byte offset (next 8-row group
+// along M/N), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// 16-byte global -> shared copy without a register round trip (both addresses
+// are 16-byte aligned: slice rows are padded to multiples of 64 elements)
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t phase) {
+  uint32_t done = 0;
+  for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(phase));
+  }
+  return done != 0;
+}
+
+// add the 64 FP32 columns of this thread's TMEM lane (accumulator at column
+// offset col) into acc[]
+__device__ __forceinline__ void drain64(uint32_t tmem_row, uint32_t col, double (&acc)[TC_BN]) {
+#pragma unroll
+  for (int c0 = 0; c0 < TC_BN; c0 += 16) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(tmem_row + col + (uint32_t)c0));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[c0 + j] += (double)__uint_as_float(r[j]);
+  }
+}
+
+struct TcArgs {
+  int m, n, kpad, nsum, batch;
+  const __nv_bfloat16* Asl;  // [batch][nsum][S][mpad][kpad]
+  const __nv_bfloat16* Bsl;  // [batch][nsum][S][npad][kpad]
+  const int* ea;             // [batch][mpad]
+  const int* eb;             // [batch][npad]
+  long long sAsl, sBsl;      // elements per (batch, term) slice set
+  int mpad, npad;
+  int kb_flags;              // K_FROM_COL / K_FROM_ROW / K_TO_COL / K_TO_ROW
+  int uplo;
+  double alpha, beta;
+  const double* Cin; int ldcin; long long sCin; int bdivC;
+  double* C; int ldc; long long sC;
+  int* err;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1 KiB alignment of the operand area
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + TC_S * TC_SLICE_A_BYTES;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.z;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  if (g.uplo == 1 && m0 > n0 + TC_BN - 1) return;
+  if (g.uplo == 2 && n0 > m0 + TC_BM - 1) return;
+  int kb = 0, ke = g.kpad;
+  if (g.kb_flags & K_FROM_COL) kb = max(kb, n0);
+  if (g.kb_flags & K_FROM_ROW) kb = max(kb, m0);
+  if (g.kb_flags & K_TO_COL) ke = min(ke, n0 + TC_BN);
+  if (g.kb_flags & K_TO_ROW) ke = min(ke, m0 + TC_BM);
+  kb = (kb / TC_BK) * TC_BK;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+  constexpr uint32_t IDESC = idesc_bf16(TC_BM, TC_BN);
+  const uint32_t mbar_addr = smem_u32(&mbar);
+
+  double acc[TC_BN];
+#pragma unroll
+  for (int j = 0; j < TC_BN; ++j) acc[j] = 0.0;
+  uint32_t phase = 0;
+  bool ok = true;
+  // accumulator a at TMEM columns [64 a, 64 a + 64): a = g - 2 for g <= 6, a = 5 for g >= 7
+  uint32_t filled = 0;  // bit a set: accumulator a holds data since its last drain
+  int chunks_since_drain = 0;
+
+  for (int js = 0; js < g.nsum && ok; ++js) {
+    const __nv_bfloat16* Ab = g.Asl + ((long long)b * g.nsum + js) * g.sAsl;
+    const __nv_bfloat16* Bb = g.Bsl + ((long long)b * g.nsum + js) * g.sBsl;
+    for (int k0 = kb; k0 < ke && ok; k0 += TC_BK) {
+      // ---- stage the 7 + 7 slices of this chunk as K-major core matrices
+      // vector v = (row, k/8): 16 bytes of 8 consecutive k
+      for (int v = tid; v < TC_S * TC_BM * (TC_BK / 8); v += TC_THREADS) {
+        const int s = v / (TC_BM * (TC_BK / 8)), rem = v % (TC_BM * (TC_BK / 8));
+        const int r = rem / (TC_BK / 8), kq = rem % (TC_BK / 8);
+        cp_async16(sA + s * TC_SLICE_A_BYTES + ((r >> 3) * (TC_BK / 8) + kq) * 128 + (r & 7) * 16,
+                   Ab + (long long)s * g.mpad * g.kpad + (long long)(m0 + r) * g.kpad + k0 + kq * 8);
+      }
+      for (int v = tid; v < TC_S * TC_BN * (TC_BK / 8); v += TC_THREADS) {
+        const int s = v / (TC_BN * (TC_BK / 8)), rem = v % (TC_BN * (TC_BK / 8));
+        const int r = rem / (TC_BK / 8), kq = rem % (TC_BK / 8);
+        cp_async16(sB + s * TC_SLICE_B_BYTES + ((r >> 3) * (TC_BK / 8) + kq) * 128 + (r & 7) * 16,
+                   Bb + (long long)s * g.npad * g.kpad + (long long)(n0 + r) * g.kpad + k0 + kq * 8);
+      }
+      asm volatile("cp.async.commit_group;");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (int s = 1; s <= TC_S; ++s)
+          for (int t = 1; t <= TC_S + 1 - s; ++t) {
+            const int gi = s + t;
+            const int a = gi <= 6 ? gi - 2 : 5;
+#pragma unroll
+            for (int ks = 0; ks < TC_BK / 16; ++ks) {
+              const uint64_t ad = smem_desc(a0 + (s - 1) * TC_SLICE_A_BYTES + ks * 256, 128, (TC_BK / 8) * 128);
+              const uint64_t bd = smem_desc(b0 + (t - 1) * TC_SLICE_B_BYTES + ks * 256, 128, (TC_BK / 8) * 128);
+              const uint32_t accum = (filled >> a) & 1u;
+              mma_bf16(tmem + (uint32_t)(a * TC_BN), ad, bd, IDESC, accum);
+              filled |= (1u << a);
+            }
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr));
+      }
+      // all threads: wait for the MMAs (they also release the staged slices)
+      ok = mbar_wait(mbar_addr, phase);
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      ++chunks_since_drain;
+      const bool last = (k0 + TC_BK >= ke) && (js + 1 == g.nsum);
+      if (ok && (chunks_since_drain * TC_BK >= 128 || last)) {
+#pragma unroll
+        for (int a = 0; a < TC_NACC - 1; ++a) drain64(tmem_row, (uint32_t)(a * TC_BN), acc);
+        if (last) drain64(tmem_row, (uint32_t)((TC_NACC - 1) * TC_BN), acc);
+        if (tid == 0) filled &= last ? 0u : (1u << (TC_NACC - 1));  // g >= 7 keeps running
+        chunks_since_drain = 0;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();  // TMEM drained / smem free before the next chunk
+    }
+  }
+  if (!ok && lane == 0) atomicExch(g.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  // ---- epilogue: scale, alpha / beta, store (row = this thread's TMEM lane)
+  const int row = m0 + warp * 32 + lane;
+  if (row >= g.m) return;
+  const int ea = g.ea[(long long)b * g.mpad + row];
+  double* C = g.C + (long long)b * g.sC;
+  const double* Cin = g.Cin ? g.Cin + (long long)(b / g.bdivC) * g.sCin : nullptr;
+#pragma unroll
+  for (int j = 0; j < TC_BN; ++j) {
+    const int col = n0 + j;
+    if (col < g.n) {
+      const int eb = g.eb[(long long)b * g.npad + col];
+      double v = g.alpha * ldexp(acc[j], ea + eb - 16);
+      if (Cin && g.beta != 0.0) v = fma(g.beta, Cin[row + (long long)col * g.ldcin], v);
+      C[row + (long long)col * g.ldc] = ok ? v : NAN;
+    }
+  }
+}
+
+// ---- slicing: exponents of rows of op(A) (cols of op(B)) then the 7 slices
+// element (i, k) of op(X) for the term j of problem b
+__device__ __forceinline__ double op_elem(const double* X, int ld, int op, int i, int k) {
+  return op == OP_N ? X[i + (long long)k * ld] : X[k + (long long)i * ld];
+}
+
+// Slicing works on 64 x 64 tiles of op(X_{b,j}) staged in shared memory, so
+// that global reads follow the memory order of X (op N: i fastest, op T: k
+// fastest) and the slice writes follow the [i][k] (k fastest) order.
+constexpr int SL_T = 64;
+
+__device__ __forceinline__ void load_tile(double (*tile)[SL_T + 1], const double* X, int ld, int op, int rows, int K,
+                                          int i0, int k0, double wj) {
+  for (int e = threadIdx.x; e < SL_T * SL_T; e += blockDim.x) {
+    // a = fastest index in memory, c = the other
+    const int a = e % SL_T, c = e / SL_T;
+    int i, k;
+    if (op == OP_N) { i = i0 + a; k = k0 + c; }
+    else { k = k0 + a; i = i0 + c; }
+    double v = 0.0;
+    if (i < rows && k < K) v = wj * (op == OP_N ? X[i + (long long)k * ld] : X[k + (long long)i * ld]);
+    tile[i - i0][k - k0] = v;
+  }
+}
+
+// exponent e_i with max |x| < 2^e_i over row i of w_j op(X_{b,j}), all terms j
+__global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX,
+                                  long long sXj, int bdiv, const double* w, int rpad, int* e) {
+  __shared__ double tile[SL_T][SL_T + 1];
+  const int i0 = blockIdx.x * SL_T, k0 = blockIdx.y * SL_T;
+  const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
+  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js]);
+  __syncthreads();
+  // 4 threads per row, then one atomic per row of the tile
+  const int r = threadIdx.x / 4, q = threadIdx.x % 4;
+  double mx = 0.0;
+  for (int k = q; k < SL_T; k += 4) mx = fmax(mx, fabs(tile[r][k]));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  if (q == 0 && mx > 0.0 && i0 + r < rows) {
+    int ex;
+    frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1)  =>  mx < 2^ex
+    atomicMax(&e[(long long)b * rpad + i0 + r], ex);
+  }
+}
+
+// slices q~_s (s = 1..7) of w_j op(X_{b,j}) 2^-e_i, stored [b][j][s][i][kpad]
+__global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX, long long sXj,
+                                int bdiv, const double* w, const int* e, int rpad, int kpad, __nv_bfloat16* out,
+                                long long sOut) {
+  __shared__ double tile[SL_T][SL_T + 1];
+  const int i0 = blockIdx.x * SL_T, k0 = blockIdx.y * SL_T;
+  const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
+  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js]);
+  __syncthreads();
+  __nv_bfloat16* o = out + ((long long)b * nsum + js) * sOut;
+  for (int t = threadIdx.x; t < SL_T * SL_T; t += blockDim.x) {
+    const int kk = t % SL_T, ii = t / SL_T;
+    const int i = i0 + ii, k = k0 + kk;
+    if (i >= rpad || k >= kpad) continue;
+    double x = (i < rows) ? ldexp(tile[ii][kk], -e[(long long)b * rpad + i]) : 0.0;
+    for (int s = 0; s < TC_S; ++s) {
+      const double y = x * 256.0;
+      const double q = rint(y);
+      x = y - q;
+      o[(long long)s * rpad * kpad + (long long)i * kpad + k] = __float2bfloat16_rn(ldexpf((float)q, -8 * s));
+    }
+  }
+}
+
+
+}  // namespace
+
+thread_local TcState t_tc;
+
+bool tc_gemm_supported(const GemmArgs<double>& g) {
+  return g.ksplit == 1 && g.m >= 1 && g.n >= 1 && g.k >= 1 && g.nsum >= 1;
+}
+
+bool tc_will_handle(const GemmArgs<double>& g) {
+  // Slicing costs O((m + n) k) memory traffic and the tile is 128 x 64 with a
+  // 64-wide k chunk: products with a short side (m < 128, n < 64 or k < 128)
+  // stay on the FP64 pipe.
+  return t_tc.enabled && t_tc.ar && ((t_tc.sites >> g.site) & 1u) && tc_gemm_supported(g) && g.m >= TC_BM &&
+         g.n >= TC_BN && g.k >= 128;
+}
+
+void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
+  ProfToken tok = prof_begin(st);  // slicing + tensor-core kernel
+  const int mpad = ceil_div(g.m, TC_BM) * TC_BM;
+  const int npad = ceil_div(g.n, TC_BN) * TC_BN;
+  const int kpad = ceil_div(g.k, TC_BK) * TC_BK;
+  const int nsum = std::max(g.nsum, 1);
+  const size_t mk = ar.mark();
+  const long long sAsl = (long long)TC_S * mpad * kpad, sBsl = (long long)TC_S * npad * kpad;
+  __nv_bfloat16* Asl = ar.get<__nv_bfloat16>((size_t)sAsl * nsum * g.batch);
+  __nv_bfloat16* Bsl = ar.get<__nv_bfloat16>((size_t)sBsl * nsum * g.batch);
+  int* ea = ar.get<int>((size_t)mpad * g.batch);
+  int* eb = ar.get<int>((size_t)npad * g.batch);
+  double* w = ar.get<double>(2 * MAX_SUM);
+  // host weights -> device (term weights apply to A; B gets unit weights)
+  double hw[2 * MAX_SUM];
+  for (int j = 0; j < MAX_SUM; ++j) { hw[j] = g.w[j]; hw[MAX_SUM + j] = 1.0; }
+  ZCSD_CUDA(cudaMemcpyAsync(w, hw, sizeof(hw), cudaMemcpyHostToDevice, st));
+  // 0xC0C0C0C0 = -1061109568: "no nonzero entry"; two of them still add up
+  // without overflow, and such rows/columns have all-zero slices
+  ZCSD_CUDA(cudaMemsetAsync(ea, 0xC0, sizeof(int) * mpad * g.batch, st));
+  ZCSD_CUDA(cudaMemsetAsync(eb, 0xC0, sizeof(int) * npad * g.batch, st));
+  // op(A): rows = m, K = k;  op(B)^T: rows = n, K = k  (op(B)^T = B^T for op N, B for op T)
+  // real data: conjugate-transpose is the transpose
+  const int opA = (g.opA == OP_N) ? OP_N : OP_T;
+  const int opBt = (g.opB == OP_N) ? OP_T : OP_N;
+  const dim3 ga(mpad / SL_T, kpad / SL_T, g.batch * nsum), gb(npad / SL_T, kpad / SL_T, g.batch * nsum);
+  tc_row_exp_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, mpad, ea);
+  ZCSD_LAUNCH();
+  tc_row_exp_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, npad, eb);
+  ZCSD_LAUNCH();
+  tc_slice_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, ea, mpad, kpad, Asl,
+                                      sAsl);
+  ZCSD_LAUNCH();
+  tc_slice_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, eb, npad,
+                                      kpad, Bsl, sBsl);
+  ZCSD_LAUNCH();
+  TcArgs t;
+  t.m = g.m; t.n = g.n; t.kpad = kpad; t.nsum = nsum; t.batch = g.batch;
+  t.Asl = Asl; t.Bsl = Bsl; t.ea = ea; t.eb = eb; t.sAsl = sAsl; t.sBsl = sBsl; t.mpad = mpad; t.npad = npad;
+  t.kb_flags = g.kflags; t.uplo = g.uplo; t.alpha = re(g.alpha); t.beta = re(g.beta);
+  t.Cin = g.Cin; t.ldcin = g.ldcin; t.sCin = g.sCin; t.bdivC = g.bdivC;
+  t.C = g.C; t.ldc = g.ldc; t.sC = g.sC; t.err = err;
+  ZCSD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  dim3 grid(mpad / TC_BM, npad / TC_BN, g.batch);
+  tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(t);
+  ZCSD_LAUNCH();
+  if (tok.slot >= 0) {
+    // FP64-equivalent multiply-add work over the tiles executed
+    double fma = 0.0;
+    for (int bx = 0; bx < mpad / TC_BM; ++bx)
+      for (int by = 0; by < npad / TC_BN; ++by) {
+        const int m0 = bx * TC_BM, n0 = by * TC_BN;
+        if (g.uplo == 1 && m0 > n0 + TC_BN - 1) continue;
+        if (g.uplo == 2 && n0 > m0 + TC_BM - 1) continue;
+        int kb = 0, ke = g.k;
+        if (g.kflags & K_FROM_COL) kb = std::max(kb, n0);
+        if (g.kflags & K_FROM_ROW) kb = std::max(kb, m0);
+        if (g.kflags & K_TO_COL) ke = std::min(ke, n0 + TC_BN);
+        if (g.kflags & K_TO_ROW) ke = std::min(ke, m0 + TC_BM);
+        if (ke > kb)
+          fma += (double)std::min(TC_BM, g.m - m0) * std::min(TC_BN, g.n - n0) * (ke - kb);
+      }
+    prof_end(tok, st, PK_TC, 2.0 * fma * nsum * g.batch, g.site);
+  }
+  ar.release(mk);
+}
+
+}  // namespace zcsd

@@ -1,0 +1,26 @@
+// FP64-accurate GEMM on the tcgen05 tensor cores by error-free BF16 slicing
+// (tc_gemm.cu).  Real FP64 only; op(A), op(B) in {N, T}.
+#pragma once
+#include "linalg.h"
+
+namespace zcsd {
+
+bool tc_gemm_supported(const GemmArgs<double>& g);
+
+// Per-call tensor-core state of the running entry point (thread-local): when
+// `enabled`, gemm<double>() sends eligible products to tc_gemm() using this
+// arena and error flag.
+struct TcState {
+  bool enabled = false;
+  unsigned sites = 0;  // bit s: GEMM call site s (GemmSite) may run on the tensor cores
+  Arena* ar = nullptr;
+  int* err = nullptr;
+};
+extern thread_local TcState t_tc;
+// true when gemm<double>(g) will run on the tensor cores
+bool tc_will_handle(const GemmArgs<double>& g);
+// C = alpha sum_j w_j op(A_j) op(B_j) + beta Cin, as gemm(); workspace for the
+// slices comes from `ar`; *err is set to 1 if a tensor-core wait timed out.
+void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err);
+
+}  // namespace zcsd
