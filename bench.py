@@ -40,7 +40,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-n", type=int, default=512, help="oracle sample size for the CPU baseline")
-    ap.add_argument("--tc", type=int, default=0, help="1: real FP64 products on the tcgen05 tensor cores (sliced BF16)")
+    ap.add_argument("--tc", type=int, default=1,
+                    help="1 (default): real FP64 products on the tcgen05 tensor cores (exact BF16 slicing); 0: FP64 pipe")
+    ap.add_argument("--compare-fp64", type=int, default=1,
+                    help="with --tc 1, also time the FP64-pipe path (same workload, same accuracy checks)")
     return ap.parse_args()
 
 
@@ -163,6 +166,67 @@ def cpu_baseline(args):
             "sample": f"oracle CSD of one n={ns} instance of the same recipe ({t:.2f} s), scaled by (n/{ns})^3"}
 
 
+def timed_run(args, B, ctx, A1, A2, out, dev, dist, local, profile):
+    """W untimed steps, then K steps between barrier + synchronize, timed with
+    CUDA events on the launching stream; returns (ms, last result, profile,
+    clocks, launches)."""
+    import torch
+
+    def step():
+        return ctx.csd_polar(A1, A2, out=out)
+
+    R = None
+    for _ in range(args.warmup):
+        R = step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if profile:
+        B.lib.csd_profile_enable(ctx._h, 1)
+    launches0 = B.lib.csd_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        R = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    launches = B.lib.csd_launch_count() - launches0
+    prof = B.csd_profile()
+    if profile:
+        B.lib.csd_profile_read(ctx._h, prof)
+        B.lib.csd_profile_enable(ctx._h, 0)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, R, prof, ck, launches
+
+
+def accuracy(R, A1, A2, th_known, n, dev):
+    """Angles against the generator's, backward error and orthogonality,
+    computed with torch on the GPU (not with the oracle)."""
+    import torch
+    rk = R["rank"]
+    th = R["theta"][:rk]
+    c, s_ = torch.cos(th), torch.sin(th)
+    U1, U2, V1 = (R[k][:, :rk] for k in ("U1", "U2", "V1"))
+    num = torch.sqrt(torch.linalg.norm(A1 - (U1 * c) @ V1.T) ** 2 + torch.linalg.norm(A2 - (U2 * s_) @ V1.T) ** 2)
+    bwd = float(num / np.sqrt(2.0 * n))  # ||A||_F = sqrt(n) for orthonormal columns
+    ang = float(np.max(np.abs(th.cpu().numpy() - th_known)))
+    # Frobenius norm (a plain reduction; the 2-norm would need torch's solver library)
+    orth = max(float(torch.linalg.norm(X.T @ X - torch.eye(rk, device=dev, dtype=X.dtype))) for X in (U1, U2, V1))
+    return {"max_abs_theta_err_vs_known": ang, "backward_err_fro_over_u": bwd / U, "orth_fro_over_u": orth / U,
+            "rank": rk}
+
+
 def main():
     args = parse()
     dist, rank, ws, local = dist_init()
@@ -192,48 +256,19 @@ def main():
     out = {k: torch.empty((n, n), dtype=torch.float64, device=dev).t() for k in ("U1", "U2", "V1")}
     out["theta"] = torch.empty(n, dtype=torch.float64, device=dev)
 
-    def step():
-        return ctx.csd_polar(A1, A2, out=out)
-
-    for _ in range(args.warmup):
-        R = step()
-    torch.cuda.synchronize()
-    # ---- timed region (device-resident inputs; A1, A2 = 256 MiB > L2)
-    stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    B.lib.csd_profile_enable(ctx._h, 1)
-    launches0 = B.lib.csd_launch_count()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0.record(stream)
-    for _ in range(args.steps):
-        R = step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    launches = B.lib.csd_launch_count() - launches0
-    prof = B.csd_profile()
-    B.lib.csd_profile_read(ctx._h, prof)
-    B.lib.csd_profile_enable(ctx._h, 0)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    # ---- headline path (inputs device-resident; A1, A2 = 256 MiB > L2)
+    ms, R, prof, ck, launches = timed_run(args, B, ctx, A1, A2, out, dev, dist, local, True)
     s_per_csd = ms / 1e3 / (args.steps * ws)
-    # ---- accuracy of the last result (torch on the GPU, not the oracle)
-    rk = R["rank"]
-    th = R["theta"][:rk]
-    c, s_ = torch.cos(th), torch.sin(th)
-    U1, U2, V1 = (R[k][:, :rk] for k in ("U1", "U2", "V1"))
-    num = torch.sqrt(torch.linalg.norm(A1 - (U1 * c) @ V1.T) ** 2 + torch.linalg.norm(A2 - (U2 * s_) @ V1.T) ** 2)
-    bwd = float(num / np.sqrt(2.0 * n))  # ||A||_F = sqrt(n) per block for orthonormal columns
-    ang = float(np.max(np.abs(th.cpu().numpy() - th_known)))
-    # Frobenius norm (a plain reduction; the 2-norm would need torch's solver library)
-    orth = max(float(torch.linalg.norm(X.T @ X - torch.eye(rk, device=dev, dtype=X.dtype))) for X in (U1, U2, V1))
+    acc = accuracy(R, A1, A2, th_known, n, dev)
+    # ---- the FP64-pipe path at the same backward-error bar, for comparison
+    fp64 = None
+    if args.tc and args.compare_fp64:
+        ctx.set_tensor_cores(False)
+        ms64, R64, _, ck64, _ = timed_run(args, B, ctx, A1, A2, out, dev, dist, local, False)
+        fp64 = {"value": ms64 / 1e3 / (args.steps * ws), "unit": "s/CSD",
+                "tflops": FLOPS_PER_CSD(n) * args.steps * ws / (ms64 / 1e3) / 1e12,
+                "accuracy": accuracy(R64, A1, A2, th_known, n, dev), "clocks": ck64}
+        ctx.set_tensor_cores(True)
     # ---- e2e: same call with pinned host buffers (copies inside the call)
     e2e = None
     if args.e2e_steps > 0:
@@ -251,28 +286,43 @@ def main():
         te = (time.perf_counter() - t0) / args.e2e_steps
         e2e = {"value": te, "unit": "s/CSD", "h2d_bytes_per_step": 2 * n * n * 8,
                "d2h_bytes_per_step": 3 * n * n * 8 + n * 8}
-    # ---- roofline of the dominant kernel (GEMM on the FP64 FMA pipe)
+    # ---- roofline of the dominant kernel
     kinds = ["gemm", "qr_panel", "potrf", "jacobi", "tc_gemm"]
     kms = {k: prof.ms[i] for i, k in enumerate(kinds)}
     dom = max(range(5), key=lambda i: prof.ms[i])
     avg_ms = prof.ms[dom] / max(prof.count[dom], 1)
     flops_per_launch = prof.flops[dom] / max(prof.count[dom], 1)
-    peak = fp64_alu_peak_tflops()
-    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+    pk = peaks()
+    if kinds[dom] == "tc_gemm":
+        # 28 BF16 slice products per FP64-equivalent product, against the
+        # measured dense BF16 peak (slicing and FP64 accumulation included in
+        # the kernel time)
+        peak = pk.get("bf16_tflops_sustained", 1719.1)
+        achieved = 28.0 * flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+        roof = {"kernel": "tc_gemm", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                "fp64_equivalent_tflops": flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0}
+    else:
+        peak = fp64_alu_peak_tflops()
+        achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+        roof = {"kernel": kinds[dom], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"}
+    products = ("tcgen05 tensor cores, exact BF16 slicing (FP64-accurate), FP64 pipe for the rest" if args.tc
+                else "FP64 FMA pipe")
     line = {
         "metric": "s/CSD at n=4096 (FP64)", "value": s_per_csd, "unit": "s/CSD", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "tflops": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12,
-        "tflops_frac_of_fp64_peak": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12 / peak,
+        "tflops_frac_of_fp64_peak": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12 / fp64_alu_peak_tflops(),
         "config": {"workload": f"real FP64 CSD n={n}, clustered theta (1/2 uniform, 1/4 within 1e-8 of 0, "
                                f"1/4 within 1e-8 of pi/2), 1e-14 noise, re-orthonormalised",
-                   "n": n, "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (2 x 128 MiB)"},
-        "accuracy": {"max_abs_theta_err_vs_known": ang, "backward_err_fro_over_u": bwd / U,
-                     "orth_fro_over_u": orth / U, "rank": rk},
-        "roofline": {"kernel": kinds[dom], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"},
+                   "n": n, "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (2 x 128 MiB)",
+                   "products": products},
+        "accuracy": acc,
+        "roofline": roof,
         "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
         "gemm_sites": {nm: {"ms_per_step": prof.site_ms[i] / args.steps,
                             "tflops": prof.site_flops[i] / max(prof.site_ms[i], 1e-9) / 1e9,
@@ -280,6 +330,8 @@ def main():
                        for i, nm in enumerate(B.csd_profile.SITES) if prof.site_count[i]},
         "clocks": ck, "gpu_launches": int(launches),
     }
+    if fp64:
+        line["fp64_pipe_path"] = fp64
     if e2e:
         line["e2e"] = e2e
     if cpu:

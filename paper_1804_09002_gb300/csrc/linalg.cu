@@ -47,67 +47,139 @@ template <class T>
 QRStore<T> qr_alloc(Arena& ar, int m, int n, int band, int batch) {
   QRStore<T> q;
   q.m = m; q.n = n; q.band = band; q.batch = batch;
-  q.npan = ceil_div(n, NB_QR);
-  q.ldy = std::max(1, std::min(m, NB_QR - 1 + band));
-  q.sY = (long long)q.npan * q.ldy * NB_QR;
-  q.sT = (long long)q.npan * NB_QR * NB_QR;
+  q.nbo = std::min(NB_OUT, ceil_div(n, NB_QR) * NB_QR);  // outer block width (small n: the whole matrix)
+  q.npan = ceil_div(n, q.nbo);
+  q.ldy = std::max(1, std::min(m, q.nbo - 1 + band));
+  q.sY = (long long)q.npan * q.ldy * q.nbo;
+  q.sT = (long long)q.npan * q.nbo * q.nbo;
   q.Y = ar.get<T>((size_t)q.sY * batch);
   q.Tf = ar.get<T>((size_t)q.sT * batch);
   return q;
 }
 
+// C <- (I - Y op(T) Y^*) C for `batch` problems: op(T) = T^* applies Q^* (the
+// factorization sweep), op(T) = T applies Q (forming Q).  Y is h x nb with
+// explicit zeros / unit diagonal, T is nb x nb upper triangular, C is h x nc.
+// W = Y^* C is split along its long K = h range when its output is small.
+template <class T>
+static void wy_apply(cudaStream_t st, Arena& ar, int h, int nc, int nb, const T* Y, int ldy, long long sY,
+                     const T* Tm, int ldt, long long sT, bool adjoint, T* C, int ldc, long long sC, int batch,
+                     int site_w, int site_w2, int site_upd) {
+  if (nc <= 0 || nb <= 0 || h <= 0) return;
+  const int kcap = std::min(nb > NB_QR ? 4 : MAX_SUM, std::max(1, h / 256));
+  const size_t mk = ar.mark();
+  const long long sW = (long long)nb * nc;
+  T* W = ar.get<T>((size_t)sW * batch * kcap);
+  T* W2 = ar.get<T>((size_t)sW * batch);
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
+  GemmArgs<T> g;  // W_s = Y^* C over K chunk s
+  g.batch = batch;
+  g.m = nb; g.n = nc; g.k = h; g.opA = OP_C; g.opB = OP_N;
+  g.A = Y; g.lda = ldy; g.sA = sY;
+  g.B = C; g.ldb = ldc; g.sB = sC;
+  g.C = W; g.ldc = nb; g.sC = sW;
+  g.site = site_w;
+  g.alpha = one; g.beta = zer;
+  const int ks = resolve_ksplit(g, std::min(kcap, pick_ksplit(nb, nc, h, batch, nb <= 32 ? 32 : 64)));
+  gemm(g, st);
+  GemmArgs<T> g2;  // W2 = op(T) sum_s W_s
+  g2.batch = batch;
+  g2.nsum = ks;
+  g2.m = nb; g2.n = nc; g2.k = nb;
+  g2.opA = adjoint ? OP_C : OP_N;
+  g2.kflags = adjoint ? K_TO_ROW : K_FROM_ROW;  // T upper triangular
+  g2.A = Tm; g2.lda = ldt; g2.sA = sT; g2.sAj = 0;
+  g2.B = W; g2.ldb = nb; g2.sB = sW * ks; g2.sBj = sW;
+  g2.C = W2; g2.ldc = nb; g2.sC = sW;
+  g2.site = site_w2;
+  g2.alpha = one; g2.beta = zer;
+  gemm(g2, st);
+  GemmArgs<T> g3;  // C -= Y W2
+  g3.batch = batch;
+  g3.m = h; g3.n = nc; g3.k = nb; g3.opA = OP_N; g3.opB = OP_N;
+  g3.A = Y; g3.lda = ldy; g3.sA = sY;
+  g3.B = W2; g3.ldb = nb; g3.sB = sW;
+  g3.Cin = C; g3.ldcin = ldc; g3.sCin = sC;
+  g3.C = C; g3.ldc = ldc; g3.sC = sC;
+  g3.site = site_upd;
+  g3.alpha = mone; g3.beta = one;
+  gemm(g3, st);
+  ar.release(mk);
+}
+
+// Two-level blocked Householder QR: outer blocks of NB_OUT columns, each
+// factored as NB_QR-wide panels (panel kernel + updates inside the block);
+// the block's compact-WY factor T (NB_OUT x NB_OUT) is merged from the panel
+// factors, T_{<i, i} = -T_{<i} (Y_{<i}^* Y_i) T_i (Q = Q_{<i} Q_i), and the
+// trailing matrix is updated once per outer block.
 template <class T>
 void qr_factor(cudaStream_t st, Arena& ar, QRStore<T>& q, T* M, int ldm, long long sM) {
   const int m = q.m, n = q.n;
   const size_t mk = ar.mark();
-  const int kmax = std::min(MAX_SUM, std::max(1, q.ldy / 256));  // largest split pick_ksplit can return
-  T* W = ar.get<T>((size_t)NB_QR * n * q.batch * kmax);
-  T* W2 = ar.get<T>((size_t)NB_QR * n * q.batch);
+  T* Tin = ar.get<T>((size_t)NB_QR * NB_QR * q.batch);
+  const int NBO = q.nbo;
+  const int scap = std::min(MAX_SUM, std::max(1, q.ldy / 256));
+  T* S = ar.get<T>((size_t)NBO * NB_QR * q.batch * scap);  // split-K parts of Y_{<i}^* Y_i
+  T* S2 = ar.get<T>((size_t)NBO * NB_QR * q.batch);
+  const long long sS = (long long)NBO * NB_QR;
   const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
-  const long long sW = (long long)NB_QR * n;  // one partial W
-  for (int p = 0; p < q.npan; ++p) {
-    const int k0 = p * NB_QR;
-    if (k0 >= m) break;
-    const int nb = std::min(NB_QR, n - k0);
-    const int h = std::min(m, k0 + nb - 1 + q.band) - k0;
-    T* Yp = q.Y + (long long)p * q.ldy * NB_QR;
-    T* Tp = q.Tf + (long long)p * NB_QR * NB_QR;
-    qr_panel<T>(st, m, n, q.band, M, ldm, sM, k0, nb, Yp, q.ldy, q.sY, Tp, q.sT, q.batch);
-    const int nc = n - (k0 + nb);
-    if (nc <= 0) continue;
-    // W = Y^* C, split along K into ks partial products W_s
-    GemmArgs<T> g;
-    g.batch = q.batch;
-    g.m = nb; g.n = nc; g.k = h; g.opA = OP_C; g.opB = OP_N;
-    g.A = Yp; g.lda = q.ldy; g.sA = q.sY;
-    g.B = M + k0 + (long long)(k0 + nb) * ldm; g.ldb = ldm; g.sB = sM;
-    g.C = W; g.ldc = NB_QR; g.sC = sW;
-    g.site = GS_QR_W;
-    const int ks = resolve_ksplit(g, pick_ksplit(nb, nc, h, q.batch, 32));
-    g.alpha = one; g.beta = zer;
-    gemm(g, st);
-    // W2 = T^* sum_s W_s   (T upper triangular: op(A)[i,k] = conj(T[k,i]) = 0 for k > i)
-    GemmArgs<T> g2;
-    g2.batch = q.batch;
-    g2.nsum = ks;
-    g2.m = nb; g2.n = nc; g2.k = nb; g2.opA = OP_C; g2.opB = OP_N;
-    g2.A = Tp; g2.lda = nb; g2.sA = q.sT; g2.sAj = 0;
-    g2.B = W; g2.ldb = NB_QR; g2.sB = sW * ks; g2.sBj = sW;
-    g2.C = W2; g2.ldc = NB_QR; g2.sC = sW;
-    g2.site = GS_QR_W2;
-    g2.alpha = one; g2.beta = zer; g2.kflags = K_TO_ROW;
-    gemm(g2, st);
-    // C -= Y W2
-    GemmArgs<T> g3;
-    g3.batch = q.batch;
-    g3.m = h; g3.n = nc; g3.k = nb; g3.opA = OP_N; g3.opB = OP_N;
-    g3.A = Yp; g3.lda = q.ldy; g3.sA = q.sY;
-    g3.B = W2; g3.ldb = NB_QR; g3.sB = (long long)NB_QR * n;
-    g3.Cin = M + k0 + (long long)(k0 + nb) * ldm; g3.ldcin = ldm; g3.sCin = sM;
-    g3.C = M + k0 + (long long)(k0 + nb) * ldm; g3.ldc = ldm; g3.sC = sM;
-    g3.site = GS_QR_UPD;
-    g3.alpha = mone; g3.beta = one;
-    gemm(g3, st);
+  for (int ob = 0; ob < q.npan; ++ob) {
+    const int K0 = ob * NBO;
+    if (K0 >= m) break;
+    const int nbo = std::min(NBO, n - K0);
+    const int hb = std::min(m, K0 + nbo - 1 + q.band) - K0;
+    T* Yb = q.Y + (long long)ob * q.ldy * NBO;
+    T* Tb = q.Tf + (long long)ob * NBO * NBO;
+    ZCSD_CUDA(cudaMemset2DAsync(Yb, sizeof(T) * q.sY, 0, sizeof(T) * (size_t)q.ldy * NBO, q.batch, st));
+    ZCSD_CUDA(cudaMemset2DAsync(Tb, sizeof(T) * q.sT, 0, sizeof(T) * (size_t)NBO * NBO, q.batch, st));
+    for (int c0 = 0; c0 < nbo; c0 += NB_QR) {
+      const int k0 = K0 + c0;
+      if (k0 >= m) break;
+      const int nb = std::min(NB_QR, nbo - c0);
+      T* Yi = Yb + c0 + (long long)c0 * q.ldy;
+      T* Ti = Tb + c0 + (long long)c0 * NBO;
+      qr_panel<T>(st, m, n, q.band, M, ldm, sM, k0, nb, Yi, q.ldy, q.sY, Tin, (long long)NB_QR * NB_QR, q.batch);
+      axpby<T>(st, nb, nb, 1.0, Tin, nb, (long long)NB_QR * NB_QR, 0.0, Ti, NBO, q.sT, q.batch);
+      if (c0 > 0) {
+        GemmArgs<T> g;  // S_s = Y_{<i}^* Y_i over K chunk s (a thin product with a long K)
+        g.batch = q.batch;
+        g.m = c0; g.n = nb; g.k = hb; g.opA = OP_C; g.opB = OP_N;
+        g.A = Yb; g.lda = q.ldy; g.sA = q.sY;
+        g.B = Yb + (long long)c0 * q.ldy; g.ldb = q.ldy; g.sB = q.sY;
+        g.C = S; g.ldc = NBO; g.sC = sS;
+        g.alpha = one; g.beta = zer;
+        const int ks = resolve_ksplit(g, std::min(scap, pick_ksplit(c0, nb, hb, q.batch, 32)));
+        gemm(g, st);
+        GemmArgs<T> g2;  // S2 = T_{<i} sum_s S_s
+        g2.batch = q.batch;
+        g2.nsum = ks;
+        g2.m = c0; g2.n = nb; g2.k = c0; g2.opA = OP_N; g2.opB = OP_N;
+        g2.A = Tb; g2.lda = NBO; g2.sA = q.sT; g2.sAj = 0;
+        g2.B = S; g2.ldb = NBO; g2.sB = sS * ks; g2.sBj = sS;
+        g2.C = S2; g2.ldc = NBO; g2.sC = sS;
+        g2.alpha = one; g2.beta = zer; g2.kflags = K_FROM_ROW;
+        gemm(g2, st);
+        GemmArgs<T> g3;  // T_{<i, i} = -S2 T_i
+        g3.batch = q.batch;
+        g3.m = c0; g3.n = nb; g3.k = nb; g3.opA = OP_N; g3.opB = OP_N;
+        g3.A = S2; g3.lda = NBO; g3.sA = sS;
+        g3.B = Ti; g3.ldb = NBO; g3.sB = q.sT;
+        g3.C = Tb + (long long)c0 * NBO; g3.ldc = NBO; g3.sC = q.sT;
+        g3.alpha = mone; g3.beta = zer; g3.kflags = K_TO_COL;
+        gemm(g3, st);
+      }
+      // update the rest of this outer block with panel i
+      const int nc_in = K0 + nbo - (k0 + nb);
+      if (nc_in > 0) {
+        const int hi = std::min(m, k0 + nb - 1 + q.band) - k0;
+        wy_apply<T>(st, ar, hi, nc_in, nb, Yi, q.ldy, q.sY, Ti, NBO, q.sT, true, M + k0 + (long long)(k0 + nb) * ldm,
+                    ldm, sM, q.batch, GS_QR_W, GS_QR_W2, GS_QR_UPD);
+      }
+    }
+    const int nc = n - (K0 + nbo);
+    if (nc > 0)
+      wy_apply<T>(st, ar, hb, nc, nbo, Yb, q.ldy, q.sY, Tb, NBO, q.sT, true, M + K0 + (long long)(K0 + nbo) * ldm,
+                  ldm, sM, q.batch, GS_QR_W, GS_QR_W2, GS_QR_UPD);
   }
   ar.release(mk);
 }
@@ -116,53 +188,17 @@ template <class T>
 void qr_form_q(cudaStream_t st, Arena& ar, const QRStore<T>& q, T* E, int lde, long long sE) {
   const int m = q.m, n = q.n;
   set_eye<T>(st, m, n, E, lde, sE, q.batch);
-  const size_t mk = ar.mark();
-  const int kmax = std::min(MAX_SUM, std::max(1, q.ldy / 256));
-  T* W = ar.get<T>((size_t)NB_QR * n * q.batch * kmax);
-  T* W2 = ar.get<T>((size_t)NB_QR * n * q.batch);
-  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
-  const long long sW = (long long)NB_QR * n;
-  for (int p = q.npan - 1; p >= 0; --p) {
-    const int k0 = p * NB_QR;
-    if (k0 >= m) continue;
-    const int nb = std::min(NB_QR, n - k0);
-    const int h = std::min(m, k0 + nb - 1 + q.band) - k0;
-    const int nc = n - k0;
-    const T* Yp = q.Y + (long long)p * q.ldy * NB_QR;
-    const T* Tp = q.Tf + (long long)p * NB_QR * NB_QR;
-    T* Es = E + k0 + (long long)k0 * lde;
-    GemmArgs<T> g;  // W = Y^* E_sub, split along K
-    g.batch = q.batch;
-    g.m = nb; g.n = nc; g.k = h; g.opA = OP_C; g.opB = OP_N;
-    g.A = Yp; g.lda = q.ldy; g.sA = q.sY;
-    g.B = Es; g.ldb = lde; g.sB = sE;
-    g.C = W; g.ldc = NB_QR; g.sC = sW;
-    g.site = GS_FQ_W;
-    const int ks = resolve_ksplit(g, pick_ksplit(nb, nc, h, q.batch, 32));
-    g.alpha = one; g.beta = zer;
-    gemm(g, st);
-    GemmArgs<T> g2;  // W2 = T sum_s W_s
-    g2.batch = q.batch;
-    g2.nsum = ks;
-    g2.m = nb; g2.n = nc; g2.k = nb; g2.opA = OP_N; g2.opB = OP_N;
-    g2.A = Tp; g2.lda = nb; g2.sA = q.sT; g2.sAj = 0;
-    g2.B = W; g2.ldb = NB_QR; g2.sB = sW * ks; g2.sBj = sW;
-    g2.C = W2; g2.ldc = NB_QR; g2.sC = sW;
-    g2.site = GS_FQ_W2;
-    g2.alpha = one; g2.beta = zer; g2.kflags = K_FROM_ROW;
-    gemm(g2, st);
-    GemmArgs<T> g3;  // E_sub -= Y W2
-    g3.batch = q.batch;
-    g3.m = h; g3.n = nc; g3.k = nb; g3.opA = OP_N; g3.opB = OP_N;
-    g3.A = Yp; g3.lda = q.ldy; g3.sA = q.sY;
-    g3.B = W2; g3.ldb = NB_QR; g3.sB = (long long)NB_QR * n;
-    g3.Cin = Es; g3.ldcin = lde; g3.sCin = sE;
-    g3.C = Es; g3.ldc = lde; g3.sC = sE;
-    g3.site = GS_FQ_UPD;
-    g3.alpha = mone; g3.beta = one;
-    gemm(g3, st);
+  const int NBO = q.nbo;
+  for (int ob = q.npan - 1; ob >= 0; --ob) {
+    const int K0 = ob * NBO;
+    if (K0 >= m) continue;
+    const int nbo = std::min(NBO, n - K0);
+    const int hb = std::min(m, K0 + nbo - 1 + q.band) - K0;
+    const T* Yb = q.Y + (long long)ob * q.ldy * NBO;
+    const T* Tb = q.Tf + (long long)ob * NBO * NBO;
+    wy_apply<T>(st, ar, hb, n - K0, nbo, Yb, q.ldy, q.sY, Tb, NBO, q.sT, false, E + K0 + (long long)K0 * lde, lde,
+                sE, q.batch, GS_FQ_W, GS_FQ_W2, GS_FQ_UPD);
   }
-  ar.release(mk);
 }
 
 template <class T>

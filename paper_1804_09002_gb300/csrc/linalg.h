@@ -9,6 +9,7 @@
 namespace zcsd {
 
 constexpr int NB_QR = 32;    // Householder panel width
+constexpr int NB_OUT = 128;  // outer block of the two-level blocked QR
 constexpr int NB_CHOL = 64;  // Cholesky / TRSM block size
 constexpr int LEAF = 64;     // Zolo-eig leaf size (Jacobi)
 
@@ -45,9 +46,9 @@ struct HostScalars {
 // explicit V panels and T factors for applying / forming Q.
 template <class T>
 struct QRStore {
-  int m = 0, n = 0, band = 0, batch = 0, npan = 0, ldy = 0;
-  T* Y = nullptr;  // per problem: npan panels of ldy x NB_QR
-  T* Tf = nullptr; // per problem: npan blocks of NB_QR x NB_QR
+  int m = 0, n = 0, band = 0, batch = 0, npan = 0, ldy = 0, nbo = 0;
+  T* Y = nullptr;  // per problem: npan outer blocks of ldy x nbo (nbo = min(NB_OUT, n rounded up to 32))
+  T* Tf = nullptr; // per problem: npan blocks of nbo x nbo
   long long sY = 0, sT = 0;
 };
 

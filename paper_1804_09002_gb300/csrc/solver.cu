@@ -673,17 +673,17 @@ size_t polar_bytes(long long n, int P, size_t es) {
   const long long nn = n * n;
   const long long r = R_MAX;
   long long qr = 2 * (2 * nn) * P * r                                         // M, E
-                 + (long long)ceil_div(n, NB_QR) * (n + 1 + NB_QR) * NB_QR * P * r  // Y
-                 + (long long)ceil_div(n, NB_QR) * NB_QR * NB_QR * P * r           // T
-                 + (long long)(MAX_SUM + 1) * NB_QR * n * P * r;                    // W (split-K parts), W2
+                 + (long long)ceil_div(n, NB_OUT) * (n + 1 + NB_OUT) * NB_OUT * P * r  // Y
+                 + (long long)ceil_div(n, NB_OUT) * NB_OUT * NB_OUT * P * r           // T
+                 + (long long)(5 * NB_OUT + (MAX_SUM + 1) * NB_QR) * n * P * r;         // W parts, W2
   long long ch = nn * P + 3 * nn * P * r + (long long)NB_CHOL * n * P * r * (2 + MAX_SUM);
   return (size_t)((2 * nn * P + std::max(qr, ch)) * es) + 64 * 256;
 }
 
 size_t heig_bytes(long long n, size_t es) {
   const long long nn = n * n;
-  long long qr = (long long)ceil_div(n, NB_QR) * (n + NB_QR) * NB_QR + (long long)ceil_div(n, NB_QR) * NB_QR * NB_QR +
-                 (long long)(MAX_SUM + 1) * NB_QR * n;
+  long long qr = (long long)ceil_div(n, NB_OUT) * (n + NB_OUT) * NB_OUT +
+                 (long long)ceil_div(n, NB_OUT) * NB_OUT * NB_OUT + (long long)(5 * NB_OUT + (MAX_SUM + 1) * NB_QR) * n;
   long long leaves = (n / 1 + 1) * 0 + (long long)LEAF * LEAF * (n / 1);
   return (size_t)((7 * nn + std::max(qr, leaves)) * es) + polar_bytes(n, 1, es) + (size_t)(3 * n + 2048) * 8 + 64 * 256;
 }
