@@ -237,71 +237,85 @@ void cholesky(cudaStream_t st, int n, T* Z, int ldz, long long sZ, T* Rinv, long
   }
 }
 
+// Recursive right-side triangular solves on column ranges [c0, c1) aligned to
+// NB_CHOL: Y R = X splits R = [R11 R12; 0 R22] into Y1 = X1 R11^{-1},
+// X2 -= Y1 R12, Y2 = X2 R22^{-1}; leaves multiply by the inverted diagonal
+// blocks.  The off-diagonal updates are n x (w/2) x (w/2) products.
+template <class T>
+static void trsm_fwd_rec(cudaStream_t st, int n, int c0, int c1, T* Yt, int ldt, long long sT, const T* Z, int ldz,
+                         long long sZ, const T* Rinv, long long sR, T* Tmp, int batch) {
+  const int w = c1 - c0;
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
+  if (w <= NB_CHOL) {
+    axpby<T>(st, n, w, 1.0, Yt + (long long)c0 * ldt, ldt, sT, 0.0, Tmp, n, (long long)n * NB_CHOL, batch);
+    GemmArgs<T> g;  // Y[:, c0:c1] = X[:, c0:c1] R_kk^{-1}
+    g.batch = batch;
+    g.m = n; g.n = w; g.k = w; g.opA = OP_N; g.opB = OP_N;
+    g.A = Tmp; g.lda = n; g.sA = (long long)n * NB_CHOL;
+    g.B = Rinv + (long long)c0 * NB_CHOL; g.ldb = NB_CHOL; g.sB = sR;
+    g.C = Yt + (long long)c0 * ldt; g.ldc = ldt; g.sC = sT;
+    g.alpha = one; g.beta = zer; g.kflags = K_TO_COL; g.site = GS_TRSM_F_DIAG;
+    gemm(g, st);
+    return;
+  }
+  const int mid = c0 + ceil_div(w / 2, NB_CHOL) * NB_CHOL;
+  trsm_fwd_rec(st, n, c0, mid, Yt, ldt, sT, Z, ldz, sZ, Rinv, sR, Tmp, batch);
+  GemmArgs<T> g;  // X2 -= Y1 R12
+  g.batch = batch;
+  g.m = n; g.n = c1 - mid; g.k = mid - c0; g.opA = OP_N; g.opB = OP_N;
+  g.A = Yt + (long long)c0 * ldt; g.lda = ldt; g.sA = sT;
+  g.B = Z + c0 + (long long)mid * ldz; g.ldb = ldz; g.sB = sZ;
+  g.Cin = Yt + (long long)mid * ldt; g.ldcin = ldt; g.sCin = sT;
+  g.C = Yt + (long long)mid * ldt; g.ldc = ldt; g.sC = sT;
+  g.alpha = mone; g.beta = one; g.site = GS_TRSM_F_UPD;
+  gemm(g, st);
+  trsm_fwd_rec(st, n, mid, c1, Yt, ldt, sT, Z, ldz, sZ, Rinv, sR, Tmp, batch);
+}
+
+// T R^* = Y with R^* lower triangular: T2 = Y2 R22^{-*}, Y1 -= T2 R12^*, T1 = Y1 R11^{-*}.
+template <class T>
+static void trsm_bwd_rec(cudaStream_t st, int n, int c0, int c1, T* Tt, int ldt, long long sT, const T* Z, int ldz,
+                         long long sZ, const T* Rinv, long long sR, T* Tmp, int batch) {
+  const int w = c1 - c0;
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
+  if (w <= NB_CHOL) {
+    axpby<T>(st, n, w, 1.0, Tt + (long long)c0 * ldt, ldt, sT, 0.0, Tmp, n, (long long)n * NB_CHOL, batch);
+    GemmArgs<T> g;  // T[:, c0:c1] = Y[:, c0:c1] R_kk^{-*}
+    g.batch = batch;
+    g.m = n; g.n = w; g.k = w; g.opA = OP_N; g.opB = OP_C;
+    g.A = Tmp; g.lda = n; g.sA = (long long)n * NB_CHOL;
+    g.B = Rinv + (long long)c0 * NB_CHOL; g.ldb = NB_CHOL; g.sB = sR;
+    g.C = Tt + (long long)c0 * ldt; g.ldc = ldt; g.sC = sT;
+    g.alpha = one; g.beta = zer; g.kflags = K_FROM_COL; g.site = GS_TRSM_B_DIAG;
+    gemm(g, st);
+    return;
+  }
+  const int mid = c0 + ceil_div(w / 2, NB_CHOL) * NB_CHOL;
+  trsm_bwd_rec(st, n, mid, c1, Tt, ldt, sT, Z, ldz, sZ, Rinv, sR, Tmp, batch);
+  GemmArgs<T> g;  // Y1 -= T2 R12^*
+  g.batch = batch;
+  g.m = n; g.n = mid - c0; g.k = c1 - mid; g.opA = OP_N; g.opB = OP_C;
+  g.A = Tt + (long long)mid * ldt; g.lda = ldt; g.sA = sT;
+  g.B = Z + c0 + (long long)mid * ldz; g.ldb = ldz; g.sB = sZ;
+  g.Cin = Tt + (long long)c0 * ldt; g.ldcin = ldt; g.sCin = sT;
+  g.C = Tt + (long long)c0 * ldt; g.ldc = ldt; g.sC = sT;
+  g.alpha = mone; g.beta = one; g.site = GS_TRSM_B_UPD;
+  gemm(g, st);
+  trsm_bwd_rec(st, n, c0, mid, Tt, ldt, sT, Z, ldz, sZ, Rinv, sR, Tmp, batch);
+}
+
 template <class T>
 void trsm_pair(cudaStream_t st, Arena& ar, int n, const T* X, int ldx, long long sX, int xdiv, const T* Z, int ldz,
                long long sZ, const T* Rinv, long long sR, T* Yt, T* Tt, int ldt, long long sT, int batch) {
   const size_t mk = ar.mark();
-  const int kmax = std::min(MAX_SUM, std::max(1, n / 256));
-  T* Tmp = ar.get<T>((size_t)n * NB_CHOL * batch * kmax);
-  const long long sTmp = (long long)n * NB_CHOL;  // one partial
-  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
-  // forward: Yt[:, k] = (X[:, k] - Yt[:, <k] R[<k, k]) R_kk^{-1}
-  for (int k0 = 0; k0 < n; k0 += NB_CHOL) {
-    const int nb = std::min(NB_CHOL, n - k0);
-    // Tmp_s = [s == 0] X[:, k] - Yt[:, K_s] R[K_s, k] over K chunks K_s of [0, k0)
-    GemmArgs<T> g;
-    g.batch = batch;
-    g.m = n; g.n = nb; g.k = k0; g.opA = OP_N; g.opB = OP_N;
-    g.A = Yt; g.lda = ldt; g.sA = sT;
-    g.B = Z + (long long)k0 * ldz; g.ldb = ldz; g.sB = sZ;
-    g.Cin = X + (long long)k0 * ldx; g.ldcin = ldx; g.sCin = sX; g.bdivC = xdiv;
-    g.C = Tmp; g.ldc = n; g.sC = sTmp;
-    g.site = GS_TRSM_F_UPD;
-    g.alpha = mone; g.beta = one;
-    if (k0 == 0) { g.k = 0; g.nsum = 0; }
-    const int ks = resolve_ksplit(g, k0 > 0 ? pick_ksplit(n, nb, k0, batch, 64) : 1);
-    gemm(g, st);
-    // Yt[:, k] = (sum_s Tmp_s) R_kk^{-1}
-    GemmArgs<T> g2;
-    g2.batch = batch;
-    g2.nsum = ks;
-    g2.m = n; g2.n = nb; g2.k = nb; g2.opA = OP_N; g2.opB = OP_N;
-    g2.A = Tmp; g2.lda = n; g2.sA = sTmp * ks; g2.sAj = sTmp;
-    g2.B = Rinv + (long long)k0 * NB_CHOL; g2.ldb = NB_CHOL; g2.sB = sR;
-    g2.C = Yt + (long long)k0 * ldt; g2.ldc = ldt; g2.sC = sT;
-    g2.site = GS_TRSM_F_DIAG;
-    g2.alpha = one; g2.beta = zer; g2.kflags = K_TO_COL;
-    gemm(g2, st);
-  }
-  // backward: Tt[:, k] = (Yt[:, k] - Tt[:, >k] R[k, >k]^*) R_kk^{-*}
-  const int nblk = ceil_div(n, NB_CHOL);
-  for (int bk = nblk - 1; bk >= 0; --bk) {
-    const int k0 = bk * NB_CHOL;
-    const int nb = std::min(NB_CHOL, n - k0);
-    const int ke = k0 + nb;
-    GemmArgs<T> g;
-    g.batch = batch;
-    g.m = n; g.n = nb; g.k = n - ke; g.opA = OP_N; g.opB = OP_C;
-    g.A = Tt + (long long)ke * ldt; g.lda = ldt; g.sA = sT;
-    g.B = Z + k0 + (long long)ke * ldz; g.ldb = ldz; g.sB = sZ;
-    g.Cin = Yt + (long long)k0 * ldt; g.ldcin = ldt; g.sCin = sT;
-    g.C = Tmp; g.ldc = n; g.sC = sTmp;
-    g.site = GS_TRSM_B_UPD;
-    g.alpha = mone; g.beta = one;
-    if (ke >= n) { g.k = 0; g.nsum = 0; }
-    const int ks = resolve_ksplit(g, ke < n ? pick_ksplit(n, nb, n - ke, batch, 64) : 1);
-    gemm(g, st);
-    GemmArgs<T> g2;
-    g2.batch = batch;
-    g2.nsum = ks;
-    g2.m = n; g2.n = nb; g2.k = nb; g2.opA = OP_N; g2.opB = OP_C;
-    g2.A = Tmp; g2.lda = n; g2.sA = sTmp * ks; g2.sAj = sTmp;
-    g2.B = Rinv + (long long)k0 * NB_CHOL; g2.ldb = NB_CHOL; g2.sB = sR;
-    g2.C = Tt + (long long)k0 * ldt; g2.ldc = ldt; g2.sC = sT;
-    g2.site = GS_TRSM_B_DIAG;
-    g2.alpha = one; g2.beta = zer; g2.kflags = K_FROM_COL;
-    gemm(g2, st);
-  }
+  T* Tmp = ar.get<T>((size_t)n * NB_CHOL * batch);
+  // Yt = X (problem b reads X_{b / xdiv}), then solve in place
+  const int P = batch / xdiv;
+  for (int j = 0; j < xdiv; ++j)
+    axpby<T>(st, n, n, 1.0, X, ldx, sX, 0.0, Yt + (long long)j * sT, ldt, sT * xdiv, P);
+  trsm_fwd_rec(st, n, 0, n, Yt, ldt, sT, Z, ldz, sZ, Rinv, sR, Tmp, batch);
+  axpby<T>(st, n, n, 1.0, Yt, ldt, sT, 0.0, Tt, ldt, sT, batch);
+  trsm_bwd_rec(st, n, 0, n, Tt, ldt, sT, Z, ldz, sZ, Rinv, sR, Tmp, batch);
   ar.release(mk);
 }
 

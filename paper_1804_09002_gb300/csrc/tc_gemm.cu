@@ -27,6 +27,8 @@
 // read their 32 TMEM lanes each with tcgen05.ld.
 #include <cuda_bf16.h>
 
+#include <climits>
+
 #include "tc_gemm.h"
 
 namespace zcsd {
@@ -244,10 +246,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
 }
 
 // ---- slicing: exponents of rows of op(A) (cols of op(B)) then the 7 slices
-// element (i, k) of op(X) for the term j of problem b
-__device__ __forceinline__ double op_elem(const double* X, int ld, int op, int i, int k) {
-  return op == OP_N ? X[i + (long long)k * ld] : X[k + (long long)i * ld];
-}
 
 // Slicing works on 64 x 64 tiles of op(X_{b,j}) staged in shared memory, so
 // that global reads follow the memory order of X (op N: i fastest, op T: k
@@ -276,17 +274,19 @@ __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const doubl
   const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
   load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js]);
   __syncthreads();
-  // 4 threads per row, then one atomic per row of the tile
+  // 4 threads per row, then one atomic per row of the tile.  The exponent
+  // is read from the bits: a normal |x| lies in [2^(E-1023), 2^(E-1022)) for
+  // biased exponent E, so E - 1022 bounds it (frexp's exponent); zeros and
+  // subnormals (E = 0) do not raise the row maximum.
   const int r = threadIdx.x / 4, q = threadIdx.x % 4;
-  double mx = 0.0;
-  for (int k = q; k < SL_T; k += 4) mx = fmax(mx, fabs(tile[r][k]));
-  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-  if (q == 0 && mx > 0.0 && i0 + r < rows) {
-    int ex;
-    frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1)  =>  mx < 2^ex
-    atomicMax(&e[(long long)b * rpad + i0 + r], ex);
+  int ex = INT_MIN;
+  for (int k = q; k < SL_T; k += 4) {
+    const int E = (int)((__double_as_longlong(tile[r][k]) >> 52) & 0x7FF);
+    if (E > 0) ex = max(ex, E - 1022);
   }
+  ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, 1));
+  ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, 2));
+  if (q == 0 && ex != INT_MIN && i0 + r < rows) atomicMax(&e[(long long)b * rpad + i0 + r], ex);
 }
 
 // slices q~_s (s = 1..7) of w_j op(X_{b,j}) 2^-e_i, stored [b][j][s][i][kpad]
@@ -303,13 +303,33 @@ __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double*
     const int kk = t % SL_T, ii = t / SL_T;
     const int i = i0 + ii, k = k0 + kk;
     if (i >= rpad || k >= kpad) continue;
-    double x = (i < rows) ? ldexp(tile[ii][kk], -e[(long long)b * rpad + i]) : 0.0;
-    for (int s = 0; s < TC_S; ++s) {
-      const double y = x * 256.0;
-      const double q = rint(y);
-      x = y - q;
-      o[(long long)s * rpad * kpad + (long long)i * kpad + k] = __float2bfloat16_rn(ldexpf((float)q, -8 * s));
+    // X = round(x 2^(56 - e_i)) as a 64-bit integer (|X| <= 2^56), then its
+    // balanced base-256 digits from the bottom: d = ((X + 128) mod 256) - 128,
+    // X <- (X - d) / 256; the top digit q_1 keeps |q_1| <= 256, the others
+    // |q_s| <= 128.  Two FP64 multiplies and one conversion per element; the
+    // rest is integer arithmetic.
+    long long X = 0;
+    const int ei = (i < rows) ? e[(long long)b * rpad + i] : INT_MIN;
+    if (ei > -2000 && tile[ii][kk] != 0.0) {  // rows without a nonzero entry keep the sentinel exponent
+      const double v = tile[ii][kk];
+      const int sh = 56 - ei;  // in [-968, 1130] for finite nonzero data
+      // 2^sh as two exact, normal powers of two
+      const int s1 = sh / 2, s2 = sh - s1;
+      X = __double2ll_rn(v * __longlong_as_double((long long)(1023 + s1) << 52) *
+                         __longlong_as_double((long long)(1023 + s2) << 52));
     }
+    int q[TC_S];
+#pragma unroll
+    for (int sidx = TC_S - 1; sidx >= 1; --sidx) {
+      const int d = (int)((X + 128) & 255) - 128;
+      q[sidx] = d;
+      X = (X - d) >> 8;
+    }
+    q[0] = (int)X;
+#pragma unroll
+    for (int sidx = 0; sidx < TC_S; ++sidx)
+      o[(long long)sidx * rpad * kpad + (long long)i * kpad + k] =
+          __float2bfloat16_rn((float)q[sidx] * __int_as_float((127 - 8 * sidx) << 23));
   }
 }
 
