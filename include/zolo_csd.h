@@ -164,7 +164,7 @@ typedef struct {
   /* GEMM launches split by call site (0 other, 1-3 QR panel update, 4-6 Q
    * formation, 7 Zolotarev term sum, 8 Gram matrix, 9-10 Cholesky, 11-14
    * triangular solves, 15 H, 16 orthogonality check, 17 Zolo-eig,
-   * 18 assembly, 19 Algorithm 2) */
+   * 18 assembly, 19 Algorithm 2, 20 merging of the blocked QR's WY factors) */
   long long site_count[24];
   double site_ms[24];
   double site_flops[24];

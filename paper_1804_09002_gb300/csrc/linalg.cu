@@ -29,16 +29,16 @@ static int pick_ksplit(int m, int n, int k, int batch, int bm, int kmin = 256) {
   return best;
 }
 
-// Products the tensor-core path takes run unsplit (it takes the whole K range).
+// Split-K factor of a product: the FP64-pipe choice `ks`, or, when the
+// tensor-core path takes the product, its own choice (one CTA per SM there);
+// both at most `cap`, the partial buffers the caller holds.
 template <class T>
-static int resolve_ksplit(GemmArgs<T>& g, int ks) {
-  g.ksplit = ks;
+static int resolve_ksplit(GemmArgs<T>& g, int ks, int cap) {
+  g.ksplit = std::max(1, std::min(ks, cap));
   if constexpr (std::is_same<T, double>::value) {
-    if (ks > 1) {
-      GemmArgs<T> probe = g;
-      probe.ksplit = 1;
-      if (tc_will_handle(probe)) g.ksplit = 1;
-    }
+    GemmArgs<T> probe = g;
+    probe.ksplit = 1;
+    if (tc_will_handle(probe)) g.ksplit = tc_pick_ksplit(probe, cap);
   }
   return g.ksplit;
 }
@@ -80,7 +80,7 @@ static void wy_apply(cudaStream_t st, Arena& ar, int h, int nc, int nb, const T*
   g.C = W; g.ldc = nb; g.sC = sW;
   g.site = site_w;
   g.alpha = one; g.beta = zer;
-  const int ks = resolve_ksplit(g, std::min(kcap, pick_ksplit(nb, nc, h, batch, nb <= 32 ? 32 : 64)));
+  const int ks = resolve_ksplit(g, pick_ksplit(nb, nc, h, batch, nb <= 32 ? 32 : 64), kcap);
   gemm(g, st);
   GemmArgs<T> g2;  // W2 = op(T) sum_s W_s
   g2.batch = batch;
@@ -119,9 +119,9 @@ void qr_factor(cudaStream_t st, Arena& ar, QRStore<T>& q, T* M, int ldm, long lo
   T* Tin = ar.get<T>((size_t)NB_QR * NB_QR * q.batch);
   const int NBO = q.nbo;
   const int scap = std::min(MAX_SUM, std::max(1, q.ldy / 256));
-  T* S = ar.get<T>((size_t)NBO * NB_QR * q.batch * scap);  // split-K parts of Y_{<i}^* Y_i
+  T* S = ar.get<T>((size_t)NBO * NBO * q.batch * scap);  // split-K parts of the Gram matrix Y_b^* Y_b
   T* S2 = ar.get<T>((size_t)NBO * NB_QR * q.batch);
-  const long long sS = (long long)NBO * NB_QR;
+  const long long sS = (long long)NBO * NBO, sS2 = (long long)NBO * NB_QR;
   const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
   for (int ob = 0; ob < q.npan; ++ob) {
     const int K0 = ob * NBO;
@@ -140,40 +140,47 @@ void qr_factor(cudaStream_t st, Arena& ar, QRStore<T>& q, T* M, int ldm, long lo
       T* Ti = Tb + c0 + (long long)c0 * NBO;
       qr_panel<T>(st, m, n, q.band, M, ldm, sM, k0, nb, Yi, q.ldy, q.sY, Tin, (long long)NB_QR * NB_QR, q.batch);
       axpby<T>(st, nb, nb, 1.0, Tin, nb, (long long)NB_QR * NB_QR, 0.0, Ti, NBO, q.sT, q.batch);
-      if (c0 > 0) {
-        GemmArgs<T> g;  // S_s = Y_{<i}^* Y_i over K chunk s (a thin product with a long K)
-        g.batch = q.batch;
-        g.m = c0; g.n = nb; g.k = hb; g.opA = OP_C; g.opB = OP_N;
-        g.A = Yb; g.lda = q.ldy; g.sA = q.sY;
-        g.B = Yb + (long long)c0 * q.ldy; g.ldb = q.ldy; g.sB = q.sY;
-        g.C = S; g.ldc = NBO; g.sC = sS;
-        g.alpha = one; g.beta = zer;
-        const int ks = resolve_ksplit(g, std::min(scap, pick_ksplit(c0, nb, hb, q.batch, 32)));
-        gemm(g, st);
-        GemmArgs<T> g2;  // S2 = T_{<i} sum_s S_s
-        g2.batch = q.batch;
-        g2.nsum = ks;
-        g2.m = c0; g2.n = nb; g2.k = c0; g2.opA = OP_N; g2.opB = OP_N;
-        g2.A = Tb; g2.lda = NBO; g2.sA = q.sT; g2.sAj = 0;
-        g2.B = S; g2.ldb = NBO; g2.sB = sS * ks; g2.sBj = sS;
-        g2.C = S2; g2.ldc = NBO; g2.sC = sS;
-        g2.alpha = one; g2.beta = zer; g2.kflags = K_FROM_ROW;
-        gemm(g2, st);
-        GemmArgs<T> g3;  // T_{<i, i} = -S2 T_i
-        g3.batch = q.batch;
-        g3.m = c0; g3.n = nb; g3.k = nb; g3.opA = OP_N; g3.opB = OP_N;
-        g3.A = S2; g3.lda = NBO; g3.sA = sS;
-        g3.B = Ti; g3.ldb = NBO; g3.sB = q.sT;
-        g3.C = Tb + (long long)c0 * NBO; g3.ldc = NBO; g3.sC = q.sT;
-        g3.alpha = mone; g3.beta = zer; g3.kflags = K_TO_COL;
-        gemm(g3, st);
-      }
       // update the rest of this outer block with panel i
       const int nc_in = K0 + nbo - (k0 + nb);
       if (nc_in > 0) {
         const int hi = std::min(m, k0 + nb - 1 + q.band) - k0;
         wy_apply<T>(st, ar, hi, nc_in, nb, Yi, q.ldy, q.sY, Ti, NBO, q.sT, true, M + k0 + (long long)(k0 + nb) * ldm,
                     ldm, sM, q.batch, GS_QR_W, GS_QR_W2, GS_QR_UPD);
+      }
+    }
+    // merge the panel factors into the block's T: one Gram matrix
+    // S = Y_b^* Y_b (split along its long K), then for each panel i,
+    // T_{<i, i} = -T_{<i} S[<i, i] T_i  (Q = Q_{<i} Q_i)
+    if (nbo > NB_QR) {
+      GemmArgs<T> g;
+      g.batch = q.batch;
+      g.m = nbo; g.n = nbo; g.k = hb; g.opA = OP_C; g.opB = OP_N;
+      g.A = Yb; g.lda = q.ldy; g.sA = q.sY;
+      g.B = Yb; g.ldb = q.ldy; g.sB = q.sY;
+      g.C = S; g.ldc = NBO; g.sC = sS;
+      g.alpha = one; g.beta = zer; g.site = GS_TMERGE;
+      const int ks = resolve_ksplit(g, pick_ksplit(nbo, nbo, hb, q.batch, 64), scap);
+      gemm(g, st);
+      for (int c0 = NB_QR; c0 < nbo; c0 += NB_QR) {
+        const int nb = std::min(NB_QR, nbo - c0);
+        T* Ti = Tb + c0 + (long long)c0 * NBO;
+        GemmArgs<T> g2;  // S2 = T_{<i} sum_s S_s[<i, i]
+        g2.batch = q.batch;
+        g2.nsum = ks;
+        g2.m = c0; g2.n = nb; g2.k = c0; g2.opA = OP_N; g2.opB = OP_N;
+        g2.A = Tb; g2.lda = NBO; g2.sA = q.sT; g2.sAj = 0;
+        g2.B = S + (long long)c0 * NBO; g2.ldb = NBO; g2.sB = sS * ks; g2.sBj = sS;
+        g2.C = S2; g2.ldc = NBO; g2.sC = sS2;
+        g2.alpha = one; g2.beta = zer; g2.kflags = K_FROM_ROW; g2.site = GS_TMERGE;
+        gemm(g2, st);
+        GemmArgs<T> g3;  // T_{<i, i} = -S2 T_i
+        g3.batch = q.batch;
+        g3.m = c0; g3.n = nb; g3.k = nb; g3.opA = OP_N; g3.opB = OP_N;
+        g3.A = S2; g3.lda = NBO; g3.sA = sS2;
+        g3.B = Ti; g3.ldb = NBO; g3.sB = q.sT;
+        g3.C = Tb + (long long)c0 * NBO; g3.ldc = NBO; g3.sC = q.sT;
+        g3.alpha = mone; g3.beta = zer; g3.kflags = K_TO_COL; g3.site = GS_TMERGE;
+        gemm(g3, st);
       }
     }
     const int nc = n - (K0 + nbo);

@@ -46,6 +46,8 @@ constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+__device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
+
 // tcgen05 shared-memory matrix descriptor: start address, leading-dimension
 // byte offset (next core matrix along K), stride byte offset (next 8-row group
 // along M/N), descriptor version 1, no swizzle.
@@ -113,6 +115,7 @@ struct TcArgs {
   long long sAsl, sBsl;      // elements per (batch, term) slice set
   int mpad, npad;
   int kb_flags;              // K_FROM_COL / K_FROM_ROW / K_TO_COL / K_TO_ROW
+  int ksplit;                // split-K parts: problem b, part s writes C_{b * ksplit + s}
   int uplo;
   double alpha, beta;
   const double* Cin; int ldcin; long long sCin; int bdivC;
@@ -129,11 +132,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.z;
+  const int z = blockIdx.z;
+  const int b = z / g.ksplit, kpart = z % g.ksplit;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
   if (g.uplo == 1 && m0 > n0 + TC_BN - 1) return;
   if (g.uplo == 2 && n0 > m0 + TC_BM - 1) return;
   int kb = 0, ke = g.kpad;
+  if (g.ksplit > 1) {  // split-K: part kpart takes one 64-aligned K range
+    const int kc = ceil_div_d(ceil_div_d(g.kpad, g.ksplit), TC_BK) * TC_BK;
+    kb = kpart * kc;
+    ke = min(g.kpad, kb + kc);
+  }
   if (g.kb_flags & K_FROM_COL) kb = max(kb, n0);
   if (g.kb_flags & K_FROM_ROW) kb = max(kb, m0);
   if (g.kb_flags & K_TO_COL) ke = min(ke, n0 + TC_BN);
@@ -231,8 +240,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   const int row = m0 + warp * 32 + lane;
   if (row >= g.m) return;
   const int ea = g.ea[(long long)b * g.mpad + row];
-  double* C = g.C + (long long)b * g.sC;
-  const double* Cin = g.Cin ? g.Cin + (long long)(b / g.bdivC) * g.sCin : nullptr;
+  double* C = g.C + (long long)z * g.sC;
+  const double* Cin = (g.Cin && kpart == 0) ? g.Cin + (long long)(b / g.bdivC) * g.sCin : nullptr;
 #pragma unroll
   for (int j = 0; j < TC_BN; ++j) {
     const int col = n0 + j;
@@ -339,7 +348,16 @@ __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double*
 thread_local TcState t_tc;
 
 bool tc_gemm_supported(const GemmArgs<double>& g) {
-  return g.ksplit == 1 && g.m >= 1 && g.n >= 1 && g.k >= 1 && g.nsum >= 1;
+  return g.ksplit >= 1 && g.m >= 1 && g.n >= 1 && g.k >= 1 && g.nsum >= 1;
+}
+
+int tc_pick_ksplit(const GemmArgs<double>& g, int cap) {
+  // one CTA per SM (shared memory and TMEM): aim at one full wave of 152
+  // CTAs, with at least 4 k chunks (256 k) per part
+  const long long tiles = (long long)ceil_div(g.m, TC_BM) * ceil_div(g.n, TC_BN) * g.batch;
+  if (tiles >= 152) return 1;
+  const int s = (int)std::min<long long>({(long long)cap, (152 + tiles - 1) / tiles, (long long)std::max(1, g.k / 256)});
+  return std::max(1, s);
 }
 
 bool tc_will_handle(const GemmArgs<double>& g) {
@@ -389,11 +407,11 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   TcArgs t;
   t.m = g.m; t.n = g.n; t.kpad = kpad; t.nsum = nsum; t.batch = g.batch;
   t.Asl = Asl; t.Bsl = Bsl; t.ea = ea; t.eb = eb; t.sAsl = sAsl; t.sBsl = sBsl; t.mpad = mpad; t.npad = npad;
-  t.kb_flags = g.kflags; t.uplo = g.uplo; t.alpha = re(g.alpha); t.beta = re(g.beta);
+  t.kb_flags = g.kflags; t.ksplit = std::max(1, g.ksplit); t.uplo = g.uplo; t.alpha = re(g.alpha); t.beta = re(g.beta);
   t.Cin = g.Cin; t.ldcin = g.ldcin; t.sCin = g.sCin; t.bdivC = g.bdivC;
   t.C = g.C; t.ldc = g.ldc; t.sC = g.sC; t.err = err;
   ZCSD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-  dim3 grid(mpad / TC_BM, npad / TC_BN, g.batch);
+  dim3 grid(mpad / TC_BM, npad / TC_BN, g.batch * t.ksplit);
   tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(t);
   ZCSD_LAUNCH();
   if (tok.slot >= 0) {

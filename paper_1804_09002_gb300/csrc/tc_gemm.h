@@ -19,6 +19,8 @@ struct TcState {
 extern thread_local TcState t_tc;
 // true when gemm<double>(g) will run on the tensor cores
 bool tc_will_handle(const GemmArgs<double>& g);
+// split-K factor (<= cap) for a product the tensor cores take
+int tc_pick_ksplit(const GemmArgs<double>& g, int cap);
 // C = alpha sum_j w_j op(A_j) op(B_j) + beta Cin, as gemm(); workspace for the
 // slices comes from `ar`; *err is set to 1 if a tensor-core wait timed out.
 void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err);
