@@ -164,7 +164,9 @@ typedef struct {
   /* GEMM launches split by call site (0 other, 1-3 QR panel update, 4-6 Q
    * formation, 7 Zolotarev term sum, 8 Gram matrix, 9-10 Cholesky, 11-14
    * triangular solves, 15 H, 16 orthogonality check, 17 Zolo-eig,
-   * 18 assembly, 19 Algorithm 2, 20 merging of the blocked QR's WY factors) */
+   * 18 assembly, 19 Algorithm 2, 20 merging of the blocked QR's WY factors,
+   * 21 rows of the dense block X in the trailing update of the stacked
+   * [X; sqrt(c) I] QR factorization; site 3 holds the rows below it) */
   long long site_count[24];
   double site_ms[24];
   double site_flops[24];
@@ -176,9 +178,10 @@ int csd_profile_enable(csd_ctx* ctx, int enable);
  * cores instead of the FP64 FMA pipe.  enable = 0 (the default) keeps every
  * product on the FP64 pipe; otherwise bit s of `enable` selects the products
  * of call site s (the site numbering of csd_profile).  enable = -1 selects
- * every site except 3 (the trailing update of the stacked QR factorization,
- * whose result needs componentwise FP64 accuracy; sliced products are
- * accurate relative to the row and column maxima of the operands).
+ * every site except 3 (the trailing update of the rows below X in the
+ * stacked [X; sqrt(c) I] QR factorization: those rows are of the size of
+ * sqrt(c) and need accuracy relative to themselves, while sliced products
+ * are accurate relative to the row and column maxima of the operands).
  * The products stay FP64-accurate: each operand is split exactly into seven
  * BF16 slices with per-row / per-column power-of-two scaling, the slice
  * products are accumulated in FP32 where that is exact and in FP64 otherwise

@@ -58,7 +58,7 @@ class csd_profile(ctypes.Structure):
 
     SITES = ["other", "qr_W", "qr_W2", "qr_update", "formq_W", "formq_W2", "formq_update", "zolo_combine",
              "gram", "chol_row", "chol_trailing", "trsm_f_update", "trsm_f_diag", "trsm_b_update",
-             "trsm_b_diag", "H", "orth", "eig", "assembly", "alg2", "tmerge"]
+             "trsm_b_diag", "H", "orth", "eig", "assembly", "alg2", "tmerge", "qr_update_x"]
 
 
 def _load():

@@ -64,7 +64,7 @@ QRStore<T> qr_alloc(Arena& ar, int m, int n, int band, int batch) {
 template <class T>
 static void wy_apply(cudaStream_t st, Arena& ar, int h, int nc, int nb, const T* Y, int ldy, long long sY,
                      const T* Tm, int ldt, long long sT, bool adjoint, T* C, int ldc, long long sC, int batch,
-                     int site_w, int site_w2, int site_upd) {
+                     int site_w, int site_w2, int site_upd, int xrows = 0) {
   if (nc <= 0 || nb <= 0 || h <= 0) return;
   const int kcap = std::min(nb > NB_QR ? 4 : MAX_SUM, std::max(1, h / 256));
   const size_t mk = ar.mark();
@@ -94,16 +94,23 @@ static void wy_apply(cudaStream_t st, Arena& ar, int h, int nc, int nb, const T*
   g2.site = site_w2;
   g2.alpha = one; g2.beta = zer;
   gemm(g2, st);
-  GemmArgs<T> g3;  // C -= Y W2
-  g3.batch = batch;
-  g3.m = h; g3.n = nc; g3.k = nb; g3.opA = OP_N; g3.opB = OP_N;
-  g3.A = Y; g3.lda = ldy; g3.sA = sY;
-  g3.B = W2; g3.ldb = nb; g3.sB = sW;
-  g3.Cin = C; g3.ldcin = ldc; g3.sCin = sC;
-  g3.C = C; g3.ldc = ldc; g3.sC = sC;
-  g3.site = site_upd;
-  g3.alpha = mone; g3.beta = one;
-  gemm(g3, st);
+  // C -= Y W2; for a stacked [X; sqrt(c) I] the rows of the X block and the
+  // rows below it are separate products (sites GS_QR_UPD_X and site_upd)
+  const int hx = std::min(std::max(xrows, 0), h);
+  for (int part = 0; part < 2; ++part) {
+    const int r0 = part == 0 ? 0 : hx, r1 = part == 0 ? hx : h;
+    if (r1 <= r0) continue;
+    GemmArgs<T> g3;
+    g3.batch = batch;
+    g3.m = r1 - r0; g3.n = nc; g3.k = nb; g3.opA = OP_N; g3.opB = OP_N;
+    g3.A = Y + r0; g3.lda = ldy; g3.sA = sY;
+    g3.B = W2; g3.ldb = nb; g3.sB = sW;
+    g3.Cin = C + r0; g3.ldcin = ldc; g3.sCin = sC;
+    g3.C = C + r0; g3.ldc = ldc; g3.sC = sC;
+    g3.site = part == 0 ? GS_QR_UPD_X : site_upd;
+    g3.alpha = mone; g3.beta = one;
+    gemm(g3, st);
+  }
   ar.release(mk);
 }
 
@@ -145,7 +152,7 @@ void qr_factor(cudaStream_t st, Arena& ar, QRStore<T>& q, T* M, int ldm, long lo
       if (nc_in > 0) {
         const int hi = std::min(m, k0 + nb - 1 + q.band) - k0;
         wy_apply<T>(st, ar, hi, nc_in, nb, Yi, q.ldy, q.sY, Ti, NBO, q.sT, true, M + k0 + (long long)(k0 + nb) * ldm,
-                    ldm, sM, q.batch, GS_QR_W, GS_QR_W2, GS_QR_UPD);
+                    ldm, sM, q.batch, GS_QR_W, GS_QR_W2, GS_QR_UPD, q.xrows - k0);
       }
     }
     // merge the panel factors into the block's T: one Gram matrix
@@ -186,7 +193,7 @@ void qr_factor(cudaStream_t st, Arena& ar, QRStore<T>& q, T* M, int ldm, long lo
     const int nc = n - (K0 + nbo);
     if (nc > 0)
       wy_apply<T>(st, ar, hb, nc, nbo, Yb, q.ldy, q.sY, Tb, NBO, q.sT, true, M + K0 + (long long)(K0 + nbo) * ldm,
-                  ldm, sM, q.batch, GS_QR_W, GS_QR_W2, GS_QR_UPD);
+                  ldm, sM, q.batch, GS_QR_W, GS_QR_W2, GS_QR_UPD, q.xrows - K0);
   }
   ar.release(mk);
 }
@@ -208,40 +215,78 @@ void qr_form_q(cudaStream_t st, Arena& ar, const QRStore<T>& q, T* E, int lde, l
   }
 }
 
+// Rows [r0, r1) of R times columns [j0, j1): Z[r0:r1, j0:j1] <- R11^{-*}
+// Z[r0:r1, j0:j1] with R11 = R[r0:r1, r0:r1] (its lower-triangular adjoint
+// solved recursively: X1 = Ra^{-*} Z1, Z2 -= Rb^* X1, X2 = Rc^{-*} Z2); leaves
+// multiply in place by the inverted diagonal block (one row tile covers it).
 template <class T>
-void cholesky(cudaStream_t st, int n, T* Z, int ldz, long long sZ, T* Rinv, long long sR, int* info, int batch) {
-  ZCSD_CUDA(cudaMemsetAsync(info, 0, sizeof(int) * batch, st));
+static void chol_row_rec(cudaStream_t st, int r0, int r1, int j0, int j1, T* Z, int ldz, long long sZ, const T* Rinv,
+                         long long sR, int batch) {
+  const int w = r1 - r0;
   const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
-  for (int k0 = 0; k0 < n; k0 += NB_CHOL) {
-    const int nb = std::min(NB_CHOL, n - k0);
-    T* Rk = Rinv + (long long)k0 * NB_CHOL;
-    potrf_inv<T>(st, n, Z, ldz, sZ, k0, nb, Rk, NB_CHOL, sR, info, batch);
-    const int nc = n - (k0 + nb);
-    if (nc <= 0) break;
-    T* Zkr = Z + k0 + (long long)(k0 + nb) * ldz;
-    // R[k, >k] = R_kk^{-*} Z[k, >k]   (in place: one row tile covers the block)
+  T* Zr = Z + r0 + (long long)j0 * ldz;
+  if (w <= NB_CHOL) {
     GemmArgs<T> g;
     g.batch = batch;
-    g.m = nb; g.n = nc; g.k = nb; g.opA = OP_C; g.opB = OP_N;
-    g.A = Rk; g.lda = NB_CHOL; g.sA = sR;
-    g.B = Zkr; g.ldb = ldz; g.sB = sZ;
-    g.C = Zkr; g.ldc = ldz; g.sC = sZ;
+    g.m = w; g.n = j1 - j0; g.k = w; g.opA = OP_C; g.opB = OP_N;
+    g.A = Rinv + (long long)r0 * NB_CHOL; g.lda = NB_CHOL; g.sA = sR;
+    g.B = Zr; g.ldb = ldz; g.sB = sZ;
+    g.C = Zr; g.ldc = ldz; g.sC = sZ;
     g.site = GS_CHOL_ROW;
     g.alpha = one; g.beta = zer; g.kflags = K_TO_ROW;
     gemm(g, st);
-    // Z[>k, >k] -= R[k, >k]^* R[k, >k]  (tiles touching the upper triangle)
-    GemmArgs<T> g2;
-    g2.batch = batch;
-    g2.m = nc; g2.n = nc; g2.k = nb; g2.opA = OP_C; g2.opB = OP_N;
-    g2.A = Zkr; g2.lda = ldz; g2.sA = sZ;
-    g2.B = Zkr; g2.ldb = ldz; g2.sB = sZ;
-    T* Ztr = Z + (k0 + nb) + (long long)(k0 + nb) * ldz;
-    g2.Cin = Ztr; g2.ldcin = ldz; g2.sCin = sZ;
-    g2.C = Ztr; g2.ldc = ldz; g2.sC = sZ;
-    g2.site = GS_CHOL_TRAIL;
-    g2.alpha = mone; g2.beta = one; g2.uplo = 1;
-    gemm(g2, st);
+    return;
   }
+  const int rm = r0 + ceil_div(w / 2, NB_CHOL) * NB_CHOL;
+  chol_row_rec(st, r0, rm, j0, j1, Z, ldz, sZ, Rinv, sR, batch);
+  GemmArgs<T> g;  // Z[rm:r1, j0:j1] -= R[r0:rm, rm:r1]^* X[r0:rm, j0:j1]
+  g.batch = batch;
+  g.m = r1 - rm; g.n = j1 - j0; g.k = rm - r0; g.opA = OP_C; g.opB = OP_N;
+  g.A = Z + r0 + (long long)rm * ldz; g.lda = ldz; g.sA = sZ;
+  g.B = Zr; g.ldb = ldz; g.sB = sZ;
+  T* Z2 = Z + rm + (long long)j0 * ldz;
+  g.Cin = Z2; g.ldcin = ldz; g.sCin = sZ;
+  g.C = Z2; g.ldc = ldz; g.sC = sZ;
+  g.site = GS_CHOL_ROW;
+  g.alpha = mone; g.beta = one;
+  gemm(g, st);
+  chol_row_rec(st, rm, r1, j0, j1, Z, ldz, sZ, Rinv, sR, batch);
+}
+
+// Recursive Cholesky Z = R^* R on [c0, c1): factor the leading half, solve
+// its rows R12 = R11^{-*} Z12, update Z22 -= R12^* R12 (one product with K =
+// half the width), factor Z22.  Leaves of NB_CHOL columns factor and invert
+// the diagonal block.
+template <class T>
+static void chol_rec(cudaStream_t st, int n, int c0, int c1, T* Z, int ldz, long long sZ, T* Rinv, long long sR,
+                     int* info, int batch) {
+  const int w = c1 - c0;
+  if (w <= NB_CHOL) {
+    potrf_inv<T>(st, n, Z, ldz, sZ, c0, w, Rinv + (long long)c0 * NB_CHOL, NB_CHOL, sR, info, batch);
+    return;
+  }
+  const int mid = c0 + ceil_div(w / 2, NB_CHOL) * NB_CHOL;
+  chol_rec(st, n, c0, mid, Z, ldz, sZ, Rinv, sR, info, batch);
+  chol_row_rec(st, c0, mid, mid, c1, Z, ldz, sZ, Rinv, sR, batch);
+  GemmArgs<T> g;  // Z22 -= R12^* R12  (tiles touching the upper triangle)
+  g.batch = batch;
+  g.m = c1 - mid; g.n = c1 - mid; g.k = mid - c0; g.opA = OP_C; g.opB = OP_N;
+  T* R12 = Z + c0 + (long long)mid * ldz;
+  g.A = R12; g.lda = ldz; g.sA = sZ;
+  g.B = R12; g.ldb = ldz; g.sB = sZ;
+  T* Z22 = Z + mid + (long long)mid * ldz;
+  g.Cin = Z22; g.ldcin = ldz; g.sCin = sZ;
+  g.C = Z22; g.ldc = ldz; g.sC = sZ;
+  g.site = GS_CHOL_TRAIL;
+  g.alpha = from_re<T>(-1.0); g.beta = from_re<T>(1.0); g.uplo = 1;
+  gemm(g, st);
+  chol_rec(st, n, mid, c1, Z, ldz, sZ, Rinv, sR, info, batch);
+}
+
+template <class T>
+void cholesky(cudaStream_t st, int n, T* Z, int ldz, long long sZ, T* Rinv, long long sR, int* info, int batch) {
+  ZCSD_CUDA(cudaMemsetAsync(info, 0, sizeof(int) * batch, st));
+  chol_rec(st, n, 0, n, Z, ldz, sZ, Rinv, sR, info, batch);
 }
 
 // Recursive right-side triangular solves on column ranges [c0, c1) aligned to

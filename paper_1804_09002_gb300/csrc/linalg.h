@@ -47,6 +47,7 @@ struct HostScalars {
 template <class T>
 struct QRStore {
   int m = 0, n = 0, band = 0, batch = 0, npan = 0, ldy = 0, nbo = 0;
+  int xrows = 0;    // rows [0, xrows) form the dense block X of a stacked [X; sqrt(c) I] (0: not stacked)
   T* Y = nullptr;  // per problem: npan outer blocks of ldy x nbo (nbo = min(NB_OUT, n rounded up to 32))
   T* Tf = nullptr; // per problem: npan blocks of nbo x nbo
   long long sY = 0, sT = 0;

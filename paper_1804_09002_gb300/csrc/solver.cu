@@ -128,6 +128,7 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd)
         T* E = ar.get<T>(sM * P * r);
         stack_terms<T>(st, n, X, n, nn, pl.sqrtc[s], r, M, m2, sM, P);
         QRStore<T> q = qr_alloc<T>(ar, m2, n, n + 1, P * r);
+        q.xrows = n;
         qr_factor<T>(st, ar, q, M, m2, sM);
         qr_form_q<T>(st, ar, q, E, m2, sM);
         // X_new = mhat X + sum_j (mhat a_j / sqrt(c_j)) Q1_j Q2_j^*   (Q2 upper triangular)
