@@ -36,13 +36,16 @@ namespace zcsd {
 namespace {
 
 constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 64, TC_S = 7;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;  // warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..
+constexpr int TC_CPT = TC_BN / 2;  // output columns per thread
 constexpr int TC_NACC = 6;          // accumulators: g = 2..6 exact, g >= 7
-constexpr int TC_TMEM_COLS = 512;   // power of two >= TC_NACC * TC_BN
+constexpr int TC_TMEM_COLS = 512;   // power of two >= TC_NACC * TC_BN + 2 * TC_BN
+constexpr int TC_ILO = TC_NACC * TC_BN, TC_IHI = TC_ILO + TC_BN;  // fixed-point sum (low / high words)
 constexpr int TC_SLICE_A_BYTES = TC_BM * TC_BK * 2;  // 16 KiB
 constexpr int TC_SLICE_B_BYTES = TC_BN * TC_BK * 2;  // 8 KiB
 constexpr int TC_SMEM = TC_S * (TC_SLICE_A_BYTES + TC_SLICE_B_BYTES) + 1024;
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;
+constexpr int TC_MAX_DRAINS = 120;  // intermediate drains before the int64 sum is written out
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -89,21 +92,70 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t phase) {
   return done != 0;
 }
 
-// add the 64 FP32 columns of this thread's TMEM lane (accumulator at column
-// offset col) into acc[]
-__device__ __forceinline__ void drain64(uint32_t tmem_row, uint32_t col, double (&acc)[TC_BN]) {
+// 16 FP32 columns of this thread's TMEM lane starting at column `col`
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(addr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
+  asm volatile("tcgen05.wait::st.sync.aligned;");
+}
+
+// The fixed-point sum I = 2^32 sum_{g=2..6} (group g) of 16 columns lives in
+// TMEM (low words at column TC_ILO, high words at TC_IHI) between drains, so
+// no registers stay live across the k loop.
+__device__ __forceinline__ void ifix_load16(uint32_t tmem_row, int c, long long (&I)[16]) {
+  uint32_t lo[16], hi[16];
+  tmem_ld16(tmem_row + (uint32_t)(TC_ILO + c), lo);
+  tmem_ld16(tmem_row + (uint32_t)(TC_IHI + c), hi);
 #pragma unroll
-  for (int c0 = 0; c0 < TC_BN; c0 += 16) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(tmem_row + col + (uint32_t)c0));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
+  for (int j = 0; j < 16; ++j) I[j] = (long long)(((unsigned long long)hi[j] << 32) | lo[j]);
+}
+
+__device__ __forceinline__ void ifix_store16(uint32_t tmem_row, int c, const long long (&I)[16]) {
+  uint32_t lo[16], hi[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[c0 + j] += (double)__uint_as_float(r[j]);
+  for (int j = 0; j < 16; ++j) {
+    lo[j] = (uint32_t)(unsigned long long)I[j];
+    hi[j] = (uint32_t)((unsigned long long)I[j] >> 32);
   }
+  tmem_st16(tmem_row + (uint32_t)(TC_ILO + c), lo);
+  tmem_st16(tmem_row + (uint32_t)(TC_IHI + c), hi);
+}
+
+// Exact groups g = 2..6 (accumulators a = g - 2) into I: accumulator a holds
+// an integer multiple of 2^-8a below 2^24 in magnitude (exact in FP32), so
+// x 2^8a and a conversion give that integer exactly, which enters I shifted
+// left by 8 (4 - a).  Integer arithmetic only: the FP64 pipe runs 2 lanes per
+// clock per SM.
+__device__ __forceinline__ void drain_exact16(uint32_t tmem_row, int c, long long (&I)[16]) {
+#pragma unroll
+  for (int a = 0; a < TC_NACC - 1; ++a) {
+    uint32_t r[16];
+    tmem_ld16(tmem_row + (uint32_t)(a * TC_BN + c), r);
+    const float up = __int_as_float((127 + 8 * a) << 23);  // 2^(8a)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) I[j] += (long long)__float2int_rn(__uint_as_float(r[j]) * up) << (8 * (4 - a));
+  }
+}
+
+// d 2^e alpha: the power of two is built from its bits when it is a normal
+// number, with the sign of alpha folded in when |alpha| = 1 (asgn = sign bit)
+__device__ __forceinline__ double scale_out(double d, int e, double alpha, bool unit, unsigned long long asgn) {
+  if (e >= -1022 && e <= 1023) {
+    const double v = d * __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) | asgn));
+    return unit ? v : alpha * v;
+  }
+  return alpha * ldexp(d, e);
 }
 
 struct TcArgs {
@@ -162,18 +214,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * TC_CPT);
+  const int cbase = n0 + (warp >> 2) * TC_CPT;  // first output column of this thread
   constexpr uint32_t IDESC = idesc_bf16(TC_BM, TC_BN);
   const uint32_t mbar_addr = smem_u32(&mbar);
 
-  double acc[TC_BN];
+  {  // fixed-point sum I = 0
+    const long long z16[16] = {};
 #pragma unroll
-  for (int j = 0; j < TC_BN; ++j) acc[j] = 0.0;
+    for (int c = 0; c < TC_CPT; c += 16) ifix_store16(tmem_row, c, z16);
+  }
   uint32_t phase = 0;
   bool ok = true;
   // accumulator a at TMEM columns [64 a, 64 a + 64): a = g - 2 for g <= 6, a = 5 for g >= 7
   uint32_t filled = 0;  // bit a set: accumulator a holds data since its last drain
-  int chunks_since_drain = 0;
+  int chunks_since_drain = 0, nchunks = 0, ndrain = 0;
+  bool flushed = false;  // a partial sum was already written to C
+  const int row = m0 + (warp & 3) * 32 + lane;
+  const int ea = row < g.m ? g.ea[(long long)b * g.mpad + row] : 0;
+  const bool aunit = g.alpha == 1.0 || g.alpha == -1.0;
+  const unsigned long long asgn = (aunit && g.alpha < 0.0) ? (1ull << 63) : 0ull;
+  double* C = g.C + (long long)z * g.sC;
+  const double* Cin = (g.Cin && kpart == 0 && g.beta != 0.0) ? g.Cin + (long long)(b / g.bdivC) * g.sCin : nullptr;
 
   for (int js = 0; js < g.nsum && ok; ++js) {
     const __nv_bfloat16* Ab = g.Asl + ((long long)b * g.nsum + js) * g.sAsl;
@@ -216,16 +278,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr));
       }
       // all threads: wait for the MMAs (they also release the staged slices)
-      ok = mbar_wait(mbar_addr, phase);
+      ok = __syncthreads_and(mbar_wait(mbar_addr, phase)) != 0;  // uniform: the TMEM accesses below are warp-collective
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;");
       ++chunks_since_drain;
+      ++nchunks;
       const bool last = (k0 + TC_BK >= ke) && (js + 1 == g.nsum);
-      if (ok && (chunks_since_drain * TC_BK >= 128 || last)) {
+      // intermediate drain of the exact groups (the final one is below); every
+      // chunk writes all six accumulators, so a drain is always followed by
+      // fresh MMAs
+      if (ok && !last && chunks_since_drain * TC_BK >= 128) {
+        // |I| grows by < 2^56.1 per drain: every TC_MAX_DRAINS drains the
+        // partial sum is written out before it can leave int64 (K > ~15k)
+        const bool flush = ++ndrain == TC_MAX_DRAINS;
 #pragma unroll
-        for (int a = 0; a < TC_NACC - 1; ++a) drain64(tmem_row, (uint32_t)(a * TC_BN), acc);
-        if (last) drain64(tmem_row, (uint32_t)((TC_NACC - 1) * TC_BN), acc);
-        if (tid == 0) filled &= last ? 0u : (1u << (TC_NACC - 1));  // g >= 7 keeps running
+        for (int c = 0; c < TC_CPT; c += 16) {
+          long long I[16];
+          ifix_load16(tmem_row, c, I);
+          drain_exact16(tmem_row, c, I);
+          if (flush) {
+            if (row < g.m)
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int col = cbase + c + j;
+                if (col < g.n) {
+                  double v = scale_out((double)I[j], ea + g.eb[(long long)b * g.npad + col] - 48, g.alpha, aunit, asgn);
+                  const long long ic = row + (long long)col * g.ldc;
+                  if (flushed) v += C[ic];
+                  else if (Cin) v = fma(g.beta, Cin[row + (long long)col * g.ldcin], v);
+                  C[ic] = v;
+                }
+              }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) I[j] = 0;
+          }
+          ifix_store16(tmem_row, c, I);
+        }
+        if (flush) {
+          flushed = true;
+          ndrain = 0;
+        }
+        if (tid == 0) filled &= (1u << (TC_NACC - 1));  // g >= 7 keeps running
         chunks_since_drain = 0;
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -233,25 +326,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
     }
   }
   if (!ok && lane == 0) atomicExch(g.err, 1);
+  // ---- final drain + epilogue, 16 columns at a time (row = this thread's
+  // TMEM lane): value = (I + 2^32 acc_{g>=7}) 2^(ea + eb - 48), then alpha,
+  // beta; about five FP64 operations per output
+  const bool have = ok && nchunks > 0;
+#pragma unroll
+  for (int c0 = 0; c0 < TC_CPT; c0 += 16) {
+    uint32_t r7[16];
+    long long I[16];
+    ifix_load16(tmem_row, c0, I);
+    if (have) {
+      drain_exact16(tmem_row, c0, I);
+      tmem_ld16(tmem_row + (uint32_t)((TC_NACC - 1) * TC_BN + c0), r7);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) r7[j] = 0u;
+    }
+    if (row < g.m) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = cbase + c0 + j;
+        if (col < g.n) {
+          const double d = (double)I[j] + (double)(__uint_as_float(r7[j]) * 4294967296.0f);
+          double v = scale_out(d, ea + g.eb[(long long)b * g.npad + col] - 48, g.alpha, aunit, asgn);
+          const long long ic = row + (long long)col * g.ldc;
+          if (flushed) v += C[ic];
+          else if (Cin) v = fma(g.beta, Cin[row + (long long)col * g.ldcin], v);
+          C[ic] = ok ? v : NAN;
+        }
+      }
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
-  // ---- epilogue: scale, alpha / beta, store (row = this thread's TMEM lane)
-  const int row = m0 + warp * 32 + lane;
-  if (row >= g.m) return;
-  const int ea = g.ea[(long long)b * g.mpad + row];
-  double* C = g.C + (long long)z * g.sC;
-  const double* Cin = (g.Cin && kpart == 0) ? g.Cin + (long long)(b / g.bdivC) * g.sCin : nullptr;
-#pragma unroll
-  for (int j = 0; j < TC_BN; ++j) {
-    const int col = n0 + j;
-    if (col < g.n) {
-      const int eb = g.eb[(long long)b * g.npad + col];
-      double v = g.alpha * ldexp(acc[j], ea + eb - 16);
-      if (Cin && g.beta != 0.0) v = fma(g.beta, Cin[row + (long long)col * g.ldcin], v);
-      C[row + (long long)col * g.ldc] = ok ? v : NAN;
-    }
-  }
 }
 
 // ---- slicing: exponents of rows of op(A) (cols of op(B)) then the 7 slices
