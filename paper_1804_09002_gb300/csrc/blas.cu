@@ -240,6 +240,17 @@ void axpby(cudaStream_t st, int m, int n, double alpha, const T* X, int ldx, lon
 }
 
 template <class T>
+void sum_parts(cudaStream_t st, int m, int n, T* X, int ldx, long long sPart, int parts, int batch) {
+  if (parts <= 1) return;
+  ew2d(st, m, n, batch, [=] __device__(int i, int j, int b) {
+    T* x = X + (long long)b * parts * sPart + i + (long long)j * ldx;
+    T acc = *x;
+    for (int s = 1; s < parts; ++s) acc = add(acc, x[s * sPart]);
+    *x = acc;
+  });
+}
+
+template <class T>
 void copy_shift(cudaStream_t st, int n, double alpha, const T* X, int ldx, long long sX, double shift, T* Y,
                 int ldy, long long sY, int batch) {
   ew2d(st, n, n, batch, [=] __device__(int i, int j, int b) {
@@ -605,6 +616,7 @@ void randn(cudaStream_t st, int m, int n, T* X, int ldx, unsigned long long seed
   template void gemm1<T>(cudaStream_t, int, int, int, int, int, T, const T*, int, const T*, int, T, T*, int, int, \
                          int, int);                                                                                \
   template void axpby<T>(cudaStream_t, int, int, double, const T*, int, long long, double, T*, int, long long, int); \
+  template void sum_parts<T>(cudaStream_t, int, int, T*, int, long long, int, int);                                  \
   template void copy_shift<T>(cudaStream_t, int, double, const T*, int, long long, double, T*, int, long long, int); \
   template void shift_terms<T>(cudaStream_t, int, const T*, int, long long, const double*, int, T*, int, long long, \
                                int);                                                                            \

@@ -82,14 +82,14 @@ static void wy_apply(cudaStream_t st, Arena& ar, int h, int nc, int nb, const T*
   g.alpha = one; g.beta = zer;
   const int ks = resolve_ksplit(g, pick_ksplit(nb, nc, h, batch, nb <= 32 ? 32 : 64), kcap);
   gemm(g, st);
-  GemmArgs<T> g2;  // W2 = op(T) sum_s W_s
+  sum_parts<T>(st, nb, nc, W, nb, sW, ks, batch);  // W_0 = sum_s W_s
+  GemmArgs<T> g2;  // W2 = op(T) W_0
   g2.batch = batch;
-  g2.nsum = ks;
   g2.m = nb; g2.n = nc; g2.k = nb;
   g2.opA = adjoint ? OP_C : OP_N;
   g2.kflags = adjoint ? K_TO_ROW : K_FROM_ROW;  // T upper triangular
-  g2.A = Tm; g2.lda = ldt; g2.sA = sT; g2.sAj = 0;
-  g2.B = W; g2.ldb = nb; g2.sB = sW * ks; g2.sBj = sW;
+  g2.A = Tm; g2.lda = ldt; g2.sA = sT;
+  g2.B = W; g2.ldb = nb; g2.sB = sW * ks;
   g2.C = W2; g2.ldc = nb; g2.sC = sW;
   g2.site = site_w2;
   g2.alpha = one; g2.beta = zer;
@@ -168,15 +168,15 @@ void qr_factor(cudaStream_t st, Arena& ar, QRStore<T>& q, T* M, int ldm, long lo
       g.alpha = one; g.beta = zer; g.site = GS_TMERGE;
       const int ks = resolve_ksplit(g, pick_ksplit(nbo, nbo, hb, q.batch, 64), scap);
       gemm(g, st);
+      sum_parts<T>(st, nbo, nbo, S, NBO, sS, ks, q.batch);  // S_0 = sum_s S_s
       for (int c0 = NB_QR; c0 < nbo; c0 += NB_QR) {
         const int nb = std::min(NB_QR, nbo - c0);
         T* Ti = Tb + c0 + (long long)c0 * NBO;
-        GemmArgs<T> g2;  // S2 = T_{<i} sum_s S_s[<i, i]
+        GemmArgs<T> g2;  // S2 = T_{<i} S_0[<i, i]
         g2.batch = q.batch;
-        g2.nsum = ks;
         g2.m = c0; g2.n = nb; g2.k = c0; g2.opA = OP_N; g2.opB = OP_N;
-        g2.A = Tb; g2.lda = NBO; g2.sA = q.sT; g2.sAj = 0;
-        g2.B = S + (long long)c0 * NBO; g2.ldb = NBO; g2.sB = sS * ks; g2.sBj = sS;
+        g2.A = Tb; g2.lda = NBO; g2.sA = q.sT;
+        g2.B = S + (long long)c0 * NBO; g2.ldb = NBO; g2.sB = sS * ks;
         g2.C = S2; g2.ldc = NBO; g2.sC = sS2;
         g2.alpha = one; g2.beta = zer; g2.kflags = K_FROM_ROW; g2.site = GS_TMERGE;
         gemm(g2, st);

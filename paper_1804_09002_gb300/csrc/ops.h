@@ -58,6 +58,9 @@ void gemm1(cudaStream_t st, int opA, int opB, int m, int n, int k, T alpha, cons
 // Y = alpha X (+ beta Y when beta != 0)
 template <class T> void axpby(cudaStream_t st, int m, int n, double alpha, const T* X, int ldx, long long sX,
                               double beta, T* Y, int ldy, long long sY, int batch);
+// X_{b parts} += sum_{s=1}^{parts-1} X_{b parts + s}: fold split-K partial
+// products (part s of problem b at X + (b parts + s) sPart) into part 0
+template <class T> void sum_parts(cudaStream_t st, int m, int n, T* X, int ldx, long long sPart, int parts, int batch);
 // Y = alpha X + diag_shift * I
 template <class T> void copy_shift(cudaStream_t st, int n, double alpha, const T* X, int ldx, long long sX,
                                    double shift, T* Y, int ldy, long long sY, int batch);

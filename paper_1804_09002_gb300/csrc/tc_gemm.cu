@@ -469,11 +469,10 @@ int tc_pick_ksplit(const GemmArgs<double>& g, int cap) {
 }
 
 bool tc_will_handle(const GemmArgs<double>& g) {
-  // Slicing costs O((m + n) k) memory traffic and the tile is 128 x 64 with a
-  // 64-wide k chunk: products with a short side (m < 128, n < 64 or k < 128)
-  // stay on the FP64 pipe.
+  // The tile is 128 x 64 with a 64-wide k chunk: products with a short side
+  // (m < 128, n < 64 or k < 64) stay on the FP64 pipe.
   return t_tc.enabled && t_tc.ar && ((t_tc.sites >> g.site) & 1u) && tc_gemm_supported(g) && g.m >= TC_BM &&
-         g.n >= TC_BN && g.k >= 128;
+         g.n >= TC_BN && g.k >= TC_BK;
 }
 
 void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
@@ -483,11 +482,16 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   const int kpad = ceil_div(g.k, TC_BK) * TC_BK;
   const int nsum = std::max(g.nsum, 1);
   const size_t mk = ar.mark();
-  const long long sAsl = (long long)TC_S * mpad * kpad, sBsl = (long long)TC_S * npad * kpad;
+  // op(A) and op(B)^T the same matrix (a Gram product Y^* Y): one set of
+  // slices and exponents serves both operands
+  bool same = g.A == g.B && g.lda == g.ldb && g.sA == g.sB && g.sAj == g.sBj && g.bdivA == g.bdivB && g.m == g.n &&
+              ((g.opA != OP_N) == (g.opB == OP_N));
+  for (int j = 0; j < nsum && same; ++j) same = g.w[j] == 1.0;
+  const long long sAsl = (long long)TC_S * mpad * kpad, sBsl = same ? sAsl : (long long)TC_S * npad * kpad;
   __nv_bfloat16* Asl = ar.get<__nv_bfloat16>((size_t)sAsl * nsum * g.batch);
-  __nv_bfloat16* Bsl = ar.get<__nv_bfloat16>((size_t)sBsl * nsum * g.batch);
+  __nv_bfloat16* Bsl = same ? Asl : ar.get<__nv_bfloat16>((size_t)sBsl * nsum * g.batch);
   int* ea = ar.get<int>((size_t)mpad * g.batch);
-  int* eb = ar.get<int>((size_t)npad * g.batch);
+  int* eb = same ? ea : ar.get<int>((size_t)npad * g.batch);
   double* w = ar.get<double>(2 * MAX_SUM);
   // host weights -> device (term weights apply to A; B gets unit weights)
   double hw[2 * MAX_SUM];
@@ -496,7 +500,7 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   // 0xC0C0C0C0 = -1061109568: "no nonzero entry"; two of them still add up
   // without overflow, and such rows/columns have all-zero slices
   ZCSD_CUDA(cudaMemsetAsync(ea, 0xC0, sizeof(int) * mpad * g.batch, st));
-  ZCSD_CUDA(cudaMemsetAsync(eb, 0xC0, sizeof(int) * npad * g.batch, st));
+  if (!same) ZCSD_CUDA(cudaMemsetAsync(eb, 0xC0, sizeof(int) * npad * g.batch, st));
   // op(A): rows = m, K = k;  op(B)^T: rows = n, K = k  (op(B)^T = B^T for op N, B for op T)
   // real data: conjugate-transpose is the transpose
   const int opA = (g.opA == OP_N) ? OP_N : OP_T;
@@ -504,17 +508,23 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   const dim3 ga(mpad / SL_T, kpad / SL_T, g.batch * nsum), gb(npad / SL_T, kpad / SL_T, g.batch * nsum);
   tc_row_exp_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, mpad, ea);
   ZCSD_LAUNCH();
-  tc_row_exp_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, npad, eb);
-  ZCSD_LAUNCH();
+  if (!same) {
+    tc_row_exp_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, npad,
+                                          eb);
+    ZCSD_LAUNCH();
+  }
   tc_slice_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, ea, mpad, kpad, Asl,
                                       sAsl);
   ZCSD_LAUNCH();
-  tc_slice_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, eb, npad,
-                                      kpad, Bsl, sBsl);
-  ZCSD_LAUNCH();
+  if (!same) {
+    tc_slice_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, eb, npad,
+                                        kpad, Bsl, sBsl);
+    ZCSD_LAUNCH();
+  }
   TcArgs t;
   t.m = g.m; t.n = g.n; t.kpad = kpad; t.nsum = nsum; t.batch = g.batch;
-  t.Asl = Asl; t.Bsl = Bsl; t.ea = ea; t.eb = eb; t.sAsl = sAsl; t.sBsl = sBsl; t.mpad = mpad; t.npad = npad;
+  t.Asl = Asl; t.Bsl = Bsl; t.ea = ea; t.eb = eb; t.sAsl = sAsl; t.sBsl = sBsl; t.mpad = mpad;
+  t.npad = same ? mpad : npad;  // row pitch of the B slices and exponents
   t.kb_flags = g.kflags; t.ksplit = std::max(1, g.ksplit); t.uplo = g.uplo; t.alpha = re(g.alpha); t.beta = re(g.beta);
   t.Cin = g.Cin; t.ldcin = g.ldcin; t.sCin = g.sCin; t.bdivC = g.bdivC;
   t.C = g.C; t.ldc = g.ldc; t.sC = g.sC; t.err = err;
