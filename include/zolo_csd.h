@@ -177,16 +177,17 @@ int csd_profile_enable(csd_ctx* ctx, int enable);
 /* Run the real FP64 matrix products of this context on the tcgen05 tensor
  * cores instead of the FP64 FMA pipe.  enable = 0 (the default) keeps every
  * product on the FP64 pipe; otherwise bit s of `enable` selects the products
- * of call site s (the site numbering of csd_profile).  enable = -1 selects
- * every site except 3 (the trailing update of the rows below X in the
- * stacked [X; sqrt(c) I] QR factorization: those rows are of the size of
- * sqrt(c) and need accuracy relative to themselves, while sliced products
- * are accurate relative to the row and column maxima of the operands).
+ * of call site s (the site numbering of csd_profile); enable = -1 selects
+ * every site.
  * The products stay FP64-accurate: each operand is split exactly into seven
  * BF16 slices with per-row / per-column power-of-two scaling, the slice
- * products are accumulated in FP32 where that is exact and in FP64 otherwise
- * (error of the same order as an FP64 product).  Complex data always uses
- * the FP64 pipe.  Returns 0 or -1 (NULL context). */
+ * products are accumulated exactly (FP32 over 128 k, then a 64-bit integer)
+ * except the smallest ones (error of the same order as an FP64 product).
+ * The rows below X in the trailing update of the stacked [X; sqrt(c) I]
+ * factorization (site 3) are of the size of sqrt(c) and need accuracy
+ * relative to themselves: that product is also balanced along its inner
+ * dimension by powers of two (A D, D^-1 B, D = diag of the row maxima of B).
+ * Complex data always uses the FP64 pipe.  Returns 0 or -1 (NULL context). */
 int csd_set_tensor_cores(csd_ctx* ctx, int enable);
 int csd_profile_read(csd_ctx* ctx, csd_profile* out);
 

@@ -108,6 +108,7 @@ static void wy_apply(cudaStream_t st, Arena& ar, int h, int nc, int nb, const T*
     g3.Cin = C + r0; g3.ldcin = ldc; g3.sCin = sC;
     g3.C = C + r0; g3.ldc = ldc; g3.sC = sC;
     g3.site = part == 0 ? GS_QR_UPD_X : site_upd;
+    g3.kbal = part == 0 ? 0 : 1;  // rows of the size of sqrt(c): balance k on the tensor cores
     g3.alpha = mone; g3.beta = one;
     gemm(g3, st);
   }

@@ -44,6 +44,7 @@ struct GemmArgs {
   int kflags = 0;
   int site = 0;                 // call-site label for kernel accounting (GemmSite)
   int ksplit = 1;               // split-K: problem b, part s writes C_{b*ksplit+s} (Cin/beta only in part 0)
+  int kbal = 0;                 // tensor-core path: balance the inner dimension by the row maxima of op(B)
   GemmArgs() { for (int i = 0; i < MAX_SUM; ++i) w[i] = 1.0; }
 };
 

@@ -944,7 +944,7 @@ int csd_set_tensor_cores(csd_ctx* ctx, int enable) {
   // trailing update C -= Y W2 of the stacked [X; sqrt(c) I] factorization is
   // excluded: it needs the componentwise accuracy of the FP64 pipe (sliced
   // products are accurate relative to row / column maxima only).
-  ctx->cx.tc_sites = enable == -1 ? ~(1u << GS_QR_UPD) : (unsigned)enable;
+  ctx->cx.tc_sites = (unsigned)enable;  // -1: every site
   return CSD_OK;
 }
 

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
 constexpr int SL_T = 64;
 
 __device__ __forceinline__ void load_tile(double (*tile)[SL_T + 1], const double* X, int ld, int op, int rows, int K,
-                                          int i0, int k0, double wj) {
+                                          int i0, int k0, double wj, const int* ek, int sgn) {
   for (int e = threadIdx.x; e < SL_T * SL_T; e += blockDim.x) {
     // a = fastest index in memory, c = the other
     const int a = e % SL_T, c = e / SL_T;
@@ -378,18 +378,26 @@ __device__ __forceinline__ void load_tile(double (*tile)[SL_T + 1], const double
     if (op == OP_N) { i = i0 + a; k = k0 + c; }
     else { k = k0 + a; i = i0 + c; }
     double v = 0.0;
-    if (i < rows && k < K) v = wj * (op == OP_N ? X[i + (long long)k * ld] : X[k + (long long)i * ld]);
+    if (i < rows && k < K) {
+      v = wj * (op == OP_N ? X[i + (long long)k * ld] : X[k + (long long)i * ld]);
+      if (ek) {  // inner-dimension balance: x 2^(sgn e_k), exact (sentinel e_k: zero row of op(B), no shift)
+        const int sh = ek[k] < -2000 ? 0 : sgn * ek[k];
+        v = (sh >= -1022 && sh <= 1023) ? v * __longlong_as_double((long long)(sh + 1023) << 52) : ldexp(v, sh);
+      }
+    }
     tile[i - i0][k - k0] = v;
   }
 }
 
 // exponent e_i with max |x| < 2^e_i over row i of w_j op(X_{b,j}), all terms j
 __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX,
-                                  long long sXj, int bdiv, const double* w, int rpad, int* e) {
+                                  long long sXj, int bdiv, const double* w, int rpad, int* e, const int* ek,
+                                  int ekpad, int sgn) {
   __shared__ double tile[SL_T][SL_T + 1];
   const int i0 = blockIdx.x * SL_T, k0 = blockIdx.y * SL_T;
   const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
-  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js]);
+  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js],
+            ek ? ek + (long long)b * ekpad : nullptr, sgn);
   __syncthreads();
   // 4 threads per row, then one atomic per row of the tile.  The exponent
   // is read from the bits: a normal |x| lies in [2^(E-1023), 2^(E-1022)) for
@@ -409,11 +417,12 @@ __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const doubl
 // slices q~_s (s = 1..7) of w_j op(X_{b,j}) 2^-e_i, stored [b][j][s][i][kpad]
 __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX, long long sXj,
                                 int bdiv, const double* w, const int* e, int rpad, int kpad, __nv_bfloat16* out,
-                                long long sOut) {
+                                long long sOut, const int* ek, int sgn) {
   __shared__ double tile[SL_T][SL_T + 1];
   const int i0 = blockIdx.x * SL_T, k0 = blockIdx.y * SL_T;
   const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
-  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js]);
+  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js],
+            ek ? ek + (long long)b * kpad : nullptr, sgn);
   __syncthreads();
   __nv_bfloat16* o = out + ((long long)b * nsum + js) * sOut;
   for (int t = threadIdx.x; t < SL_T * SL_T; t += blockDim.x) {
@@ -506,19 +515,33 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   const int opA = (g.opA == OP_N) ? OP_N : OP_T;
   const int opBt = (g.opB == OP_N) ? OP_T : OP_N;
   const dim3 ga(mpad / SL_T, kpad / SL_T, g.batch * nsum), gb(npad / SL_T, kpad / SL_T, g.batch * nsum);
-  tc_row_exp_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, mpad, ea);
+  // inner-dimension balance (one term only): e_k bounds row k of op(B);
+  // op(A) D and D^-1 op(B) with D = diag(2^e_k) have the same product, and
+  // per-row / per-column slicing of the balanced operands is accurate
+  // relative to max_k |a_ik| |b_k.| instead of max |a_i.| max |b_.j|
+  int* ek = nullptr;
+  if (g.kbal && nsum == 1 && !same) {
+    ek = ar.get<int>((size_t)kpad * g.batch);
+    ZCSD_CUDA(cudaMemsetAsync(ek, 0xC0, sizeof(int) * kpad * g.batch, st));
+    const dim3 gk(kpad / SL_T, ceil_div(g.n, SL_T), g.batch);
+    tc_row_exp_kernel<<<gk, 256, 0, st>>>(g.k, g.n, 1, g.opB == OP_N ? OP_N : OP_T, g.B, g.ldb, g.sB, 0, g.bdivB,
+                                          w + MAX_SUM, kpad, ek, nullptr, 0, 0);
+    ZCSD_LAUNCH();
+  }
+  tc_row_exp_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, mpad, ea, ek, kpad,
+                                        1);
   ZCSD_LAUNCH();
   if (!same) {
     tc_row_exp_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, npad,
-                                          eb);
+                                          eb, ek, kpad, -1);
     ZCSD_LAUNCH();
   }
   tc_slice_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, ea, mpad, kpad, Asl,
-                                      sAsl);
+                                      sAsl, ek, 1);
   ZCSD_LAUNCH();
   if (!same) {
     tc_slice_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, eb, npad,
-                                        kpad, Bsl, sBsl);
+                                        kpad, Bsl, sBsl, ek, -1);
     ZCSD_LAUNCH();
   }
   TcArgs t;

@@ -103,3 +103,15 @@ def test_tc_csd_full_size_n4096(C):
     assert np.max(np.abs(got - th)) <= 1e-12 * n
     assert be <= 50 * n * U
     assert orth <= 50 * n * U
+
+
+@pytest.mark.parametrize("kind,n", [(2, 339), (4, 480)])
+def test_tc_csd_section6_families(C, kind, n):
+    # family 2: angles spread over 18 orders of magnitude; family 4: the same
+    # with a quarter of the indices rank-deficient.  The stacked-QR rows below
+    # X need the inner-dimension balance on the tensor cores (without it,
+    # family 4 at n = 480 lost all accuracy)
+    A1, A2 = I.paper_test(kind, n, seed=kind, cplx=False)
+    R = C.csd_polar(to_dev(A1), to_dev(A2))
+    ref = O.csd(A1, A2)
+    _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=ref["rank"])
