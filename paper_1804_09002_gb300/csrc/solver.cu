@@ -470,10 +470,9 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     info->orth_err[1] = orth[1];
     info->chol_fallback = pd.chol_fallback;
   }
-  const double orth_tol = 50.0 * n * U_ROUND;
-  for (int i = 0; i < 2 && mu == 0.0; ++i) {
-    if (orth[i] <= orth_tol) continue;
-    // Algorithm 2: A_i = Q_i R_i, H_i = Q~ R~, W_i = Q_i Q~^* (diag(R) >= 0)
+  // Algorithm 2, lines 2-3, for block i: A_i = Q_i R_i, H_i = Q~ R~,
+  // W_i = Q_i Q~^* (diag(R) >= 0); H_i is kept
+  auto alg2 = [&](int i) {
     const size_t mk = ar.mark();
     T* Ma = ar.get<T>(nn);
     T* Mh = ar.get<T>(nn);
@@ -504,15 +503,16 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     rdiff_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, Ma, n, d1, Mh, n, d2, D);
     ZCSD_LAUNCH();
     fro2<T>(st, n, n, D, n, 0, 0.0, sc + 8, 1, scratch);
-    rdiff_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, Ma, n, d1, Ma, n, d1, D);  // zero; reuse for ||R||
-    ZCSD_LAUNCH();
-    fro2<T>(st, n, n, Ma, n, 0, 0.0, sc + 9, 1, scratch);  // ||R|| + ||V below||: upper bound
-    d2h(cx, cx.hs.d, sc + 8, 2 * sizeof(double));
+    d2h(cx, cx.hs.d, sc + 8, sizeof(double));
     const double rd = std::sqrt(cx.hs.d[0]) / std::max(std::sqrt(fro / 2.0), 1e-300);
     if (info) { info->alg2_used[i] = 1; info->rdiff[i] = rd; }
     if (rd > 1e3 * n * U_ROUND) status = CSD_WARN_ALG2_RCHECK;
     ar.release(mk);
-  }
+  };
+  // full rank: Algorithm 2 where W_i is not orthonormal
+  const double orth_tol = 50.0 * n * U_ROUND;
+  for (int i = 0; i < 2 && mu == 0.0; ++i)
+    if (orth[i] > orth_tol) alg2(i);
   // ---- line 4: B = H2 - H1 + mu (I - A^* A)
   {
     const size_t mk = ar.mark();
@@ -545,28 +545,56 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     info->eig_leaves = ed.leaves;
     info->eig_offblock = ed.offblock;
   }
-  // ---- lines 6-9: U_i = W_i V1, C/S = diag(V1^* H_i V1), theta = atan2(S, C)
+  // ---- lines 6-9: C/S = diag(V1^* H_i V1), U_i = W_i V1, theta = atan2(S, C)
   T* Vr = V + (long long)lo * n;
   if (rk > 0) {
-    GemmArgs<T> g;
+    GemmArgs<T> g;  // H_i V1 (into Ut, overwritten by U_i below)
     g.batch = 2;
     g.m = n; g.n = rk; g.k = n; g.opA = OP_N; g.opB = OP_N;
-    g.A = W; g.lda = n; g.sA = nn;
+    g.A = H; g.lda = n; g.sA = nn;
     g.B = Vr; g.ldb = n; g.sB = 0;
     g.C = Ut; g.ldc = n; g.sC = nn;
     g.alpha = one; g.beta = zer;
     g.site = GS_ASSEMBLY;
     gemm(g, st);
-    T* HV = W;  // W no longer needed
-    GemmArgs<T> g2 = g;
-    g2.A = H;
-    g2.C = HV;
-    gemm(g2, st);
     double* Cd = dv;
     double* Sd = dv + n;
     double* th = dv + 2 * n;
-    col_dots<T>(st, n, rk, Vr, n, HV, n, Cd);
-    col_dots<T>(st, n, rk, Vr, n, HV + nn, n, Sd);
+    col_dots<T>(st, n, rk, Vr, n, Ut, n, Cd);
+    col_dots<T>(st, n, rk, Vr, n, Ut + nn, n, Sd);
+    g.A = W;  // U_i = W_i V1
+    gemm(g, st);
+    if (mu != 0.0) {
+      // rank-deficient and C or S ill conditioned (Section 5.2, last
+      // paragraph): the modified Zolo-pd's W_i is not orthonormal, and where
+      // a kept angle's cosine / sine is small W_i V1 loses orthonormality
+      // too.  Check U_i^* U_i = I (the tolerance of the full-rank W_i check);
+      // a block that fails takes W_i from Algorithm 2, lines 2-3.
+      const size_t mk = ar.mark();
+      T* Gu = ar.get<T>(2 * (size_t)rk * rk);
+      GemmArgs<T> gg;
+      gg.batch = 2;
+      gg.m = rk; gg.n = rk; gg.k = n; gg.opA = OP_C; gg.opB = OP_N;
+      gg.A = Ut; gg.lda = n; gg.sA = nn;
+      gg.B = Ut; gg.ldb = n; gg.sB = nn;
+      gg.C = Gu; gg.ldc = rk; gg.sC = (long long)rk * rk;
+      gg.alpha = one; gg.beta = zer;
+      gg.site = GS_ORTH;
+      gemm(gg, st);
+      fro2<T>(st, rk, rk, Gu, rk, (long long)rk * rk, 1.0, sc + 12, 2, scratch);
+      d2h(cx, cx.hs.d, sc + 12, 2 * sizeof(double));
+      ar.release(mk);
+      const double ou[2] = {std::sqrt(cx.hs.d[0]), std::sqrt(cx.hs.d[1])};
+      for (int i = 0; i < 2; ++i) {
+        if (ou[i] <= orth_tol) continue;
+        alg2(i);
+        GemmArgs<T> gi = g;
+        gi.batch = 1;
+        gi.A = W + i * nn;
+        gi.C = Ut + i * nn;
+        gemm(gi, st);
+      }
+    }
     theta_from_cs(st, rk, Cd, Sd, th);
     sort_perm(st, rk, th, perm);
     gather_vec(st, rk, th, perm, theta);

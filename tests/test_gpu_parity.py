@@ -288,3 +288,33 @@ def test_csd_algorithm2_exact_zero_angles(B):
     ref = O.csd(A1, A2)
     _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=n)
     assert np.max(np.abs(to_host(R["theta"]) - np.sort(theta))) <= 1e-12 * n
+
+
+@pytest.mark.parametrize("kind,n,seed", [(2, 339, 2), (4, 339, 4), (4, 480, 5)])
+def test_csd_section6_families(B, kind, n, seed):
+    """Section 6 families 2 and 4 (angles over 18 orders of magnitude; family
+    4 rank-deficient).  A kept angle with sine (or cosine) below eps in the
+    rank-deficient case needs Algorithm 2's W_i (Section 5.2, last
+    paragraph): without it U_2 lost orthogonality (|U_2^* U_2 - I| ~ 0.3)."""
+    A1, A2 = I.paper_test(kind, n, seed=seed, cplx=False)
+    R = B.csd_polar(to_dev(A1), to_dev(A2))
+    ref = O.csd(A1, A2)
+    if kind == 4:
+        assert R["info"]["mu"] == 2.0 and max(R["info"]["alg2_used"]) == 1
+    _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=ref["rank"])
+
+
+def test_csd_rank_deficient_kept_zero_sine(B):
+    """Rank-deficient input whose kept angles include sines below eps: W_2
+    from Algorithm 2 keeps U_2 orthonormal."""
+    n, k = 96, 72
+    rng = np.random.default_rng(91)
+    theta = rng.uniform(0, np.pi / 2, n)
+    theta[:4] = 10.0 ** rng.uniform(-19, -16, 4)
+    mask = np.ones(n, bool)
+    mask[rng.permutation(np.arange(4, n))[: n - k]] = False
+    A1, A2 = I.from_angles(theta, rng, mask=mask)
+    R = B.csd_polar(to_dev(A1), to_dev(A2))
+    assert R["info"]["mu"] == 2.0 and R["info"]["alg2_used"][1] == 1
+    ref = O.csd(A1, A2)
+    _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=k)
