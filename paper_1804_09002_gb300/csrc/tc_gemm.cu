@@ -35,15 +35,17 @@ namespace zcsd {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 64, TC_S = 7;
+constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 32, TC_S = 7;  // TC_BK: k per pipeline stage
+constexpr int TC_KALIGN = 64;  // slices are padded along k to the slicing tile
 constexpr int TC_THREADS = 256;  // warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..
 constexpr int TC_CPT = TC_BN / 2;  // output columns per thread
 constexpr int TC_NACC = 6;          // accumulators: g = 2..6 exact, g >= 7
 constexpr int TC_TMEM_COLS = 512;   // power of two >= TC_NACC * TC_BN + 2 * TC_BN
 constexpr int TC_ILO = TC_NACC * TC_BN, TC_IHI = TC_ILO + TC_BN;  // fixed-point sum (low / high words)
-constexpr int TC_SLICE_A_BYTES = TC_BM * TC_BK * 2;  // 16 KiB
-constexpr int TC_SLICE_B_BYTES = TC_BN * TC_BK * 2;  // 8 KiB
-constexpr int TC_SMEM = TC_S * (TC_SLICE_A_BYTES + TC_SLICE_B_BYTES) + 1024;
+constexpr int TC_SLICE_A_BYTES = TC_BM * TC_BK * 2;  // 8 KiB
+constexpr int TC_SLICE_B_BYTES = TC_BN * TC_BK * 2;  // 4 KiB
+constexpr int TC_STAGE_A = TC_S * TC_SLICE_A_BYTES, TC_STAGE_B = TC_S * TC_SLICE_B_BYTES;
+constexpr int TC_SMEM = 2 * (TC_STAGE_A + TC_STAGE_B) + 1024;  // two stages
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 constexpr int TC_MAX_DRAINS = 120;  // intermediate drains before the int64 sum is written out
 
@@ -148,6 +150,30 @@ __device__ __forceinline__ void drain_exact16(uint32_t tmem_row, int c, long lon
   }
 }
 
+// J 2^e as a double, rounded to nearest (ties to even on J's bits), built with
+// integer instructions: GB300's FP64 pipe retires 2 lanes per clock per SM,
+// so the epilogue keeps FP64 work to the beta C term.  Results outside the
+// normal range take ldexp.
+__device__ __forceinline__ double fix_to_double(long long J, int e) {
+  if (J == 0) return 0.0;
+  const unsigned long long sgn = J < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long mag = J < 0 ? 0ull - (unsigned long long)J : (unsigned long long)J;
+  const int lz = __clzll((long long)mag);
+  const unsigned long long m = mag << lz;  // bit 63 set: J = m 2^-lz
+  unsigned long long mant = m >> 11;       // 53 bits with the leading one
+  const unsigned long long rem = m & 0x7FFull;
+  int E = 63 - lz + e;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++E;
+    }
+  }
+  if (E < -1022 || E > 1023) return ldexp((double)J, e);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // d 2^e alpha: the power of two is built from its bits when it is a normal
 // number, with the sign of alpha folded in when |alpha| = 1 (asgn = sign bit)
 __device__ __forceinline__ double scale_out(double d, int e, double alpha, bool unit, unsigned long long asgn) {
@@ -180,8 +206,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   // 1 KiB alignment of the operand area
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
-  unsigned char* sB = smem + TC_S * TC_SLICE_A_BYTES;
-  __shared__ __align__(8) uint64_t mbar;
+  unsigned char* sB = smem + 2 * TC_STAGE_A;
+  __shared__ __align__(8) uint64_t mbar[2];  // MMA completion of the stage in buffer 0 / 1
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int z = blockIdx.z;
@@ -202,7 +228,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   kb = (kb / TC_BK) * TC_BK;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -217,14 +244,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * TC_CPT);
   const int cbase = n0 + (warp >> 2) * TC_CPT;  // first output column of this thread
   constexpr uint32_t IDESC = idesc_bf16(TC_BM, TC_BN);
-  const uint32_t mbar_addr = smem_u32(&mbar);
+  const uint32_t mbar_addr[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
 
   {  // fixed-point sum I = 0
     const long long z16[16] = {};
 #pragma unroll
     for (int c = 0; c < TC_CPT; c += 16) ifix_store16(tmem_row, c, z16);
   }
-  uint32_t phase = 0;
   bool ok = true;
   // accumulator a at TMEM columns [64 a, 64 a + 64): a = g - 2 for g <= 6, a = 5 for g >= 7
   uint32_t filled = 0;  // bit a set: accumulator a holds data since its last drain
@@ -237,57 +263,83 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   double* C = g.C + (long long)z * g.sC;
   const double* Cin = (g.Cin && kpart == 0 && g.beta != 0.0) ? g.Cin + (long long)(b / g.bdivC) * g.sCin : nullptr;
 
-  for (int js = 0; js < g.nsum && ok; ++js) {
+  // stages q = 0 .. Q-1: term js = q / nst, k range [kb + 32 (q % nst), +32);
+  // the slices of stage q + 1 load (cp.async) into the other buffer while
+  // the MMAs of stage q run; a buffer is refilled once the MMAs that read it
+  // have signalled their mbarrier
+  const int nst = ke > kb ? (ke - kb + TC_BK - 1) / TC_BK : 0;
+  const int Q = g.nsum * nst;
+  auto load_stage = [&](int q, int buf) {
+    const int js = q / nst, k0 = kb + (q % nst) * TC_BK;
     const __nv_bfloat16* Ab = g.Asl + ((long long)b * g.nsum + js) * g.sAsl;
     const __nv_bfloat16* Bb = g.Bsl + ((long long)b * g.nsum + js) * g.sBsl;
-    for (int k0 = kb; k0 < ke && ok; k0 += TC_BK) {
-      // ---- stage the 7 + 7 slices of this chunk as K-major core matrices
-      // vector v = (row, k/8): 16 bytes of 8 consecutive k
-      for (int v = tid; v < TC_S * TC_BM * (TC_BK / 8); v += TC_THREADS) {
-        const int s = v / (TC_BM * (TC_BK / 8)), rem = v % (TC_BM * (TC_BK / 8));
-        const int r = rem / (TC_BK / 8), kq = rem % (TC_BK / 8);
-        cp_async16(sA + s * TC_SLICE_A_BYTES + ((r >> 3) * (TC_BK / 8) + kq) * 128 + (r & 7) * 16,
-                   Ab + (long long)s * g.mpad * g.kpad + (long long)(m0 + r) * g.kpad + k0 + kq * 8);
-      }
-      for (int v = tid; v < TC_S * TC_BN * (TC_BK / 8); v += TC_THREADS) {
-        const int s = v / (TC_BN * (TC_BK / 8)), rem = v % (TC_BN * (TC_BK / 8));
-        const int r = rem / (TC_BK / 8), kq = rem % (TC_BK / 8);
-        cp_async16(sB + s * TC_SLICE_B_BYTES + ((r >> 3) * (TC_BK / 8) + kq) * 128 + (r & 7) * 16,
-                   Bb + (long long)s * g.npad * g.kpad + (long long)(n0 + r) * g.kpad + k0 + kq * 8);
-      }
-      asm volatile("cp.async.commit_group;");
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        for (int s = 1; s <= TC_S; ++s)
-          for (int t = 1; t <= TC_S + 1 - s; ++t) {
-            const int gi = s + t;
-            const int a = gi <= 6 ? gi - 2 : 5;
-#pragma unroll
-            for (int ks = 0; ks < TC_BK / 16; ++ks) {
-              const uint64_t ad = smem_desc(a0 + (s - 1) * TC_SLICE_A_BYTES + ks * 256, 128, (TC_BK / 8) * 128);
-              const uint64_t bd = smem_desc(b0 + (t - 1) * TC_SLICE_B_BYTES + ks * 256, 128, (TC_BK / 8) * 128);
-              const uint32_t accum = (filled >> a) & 1u;
-              mma_bf16(tmem + (uint32_t)(a * TC_BN), ad, bd, IDESC, accum);
-              filled |= (1u << a);
-            }
-          }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr));
-      }
-      // all threads: wait for the MMAs (they also release the staged slices)
-      ok = __syncthreads_and(mbar_wait(mbar_addr, phase)) != 0;  // uniform: the TMEM accesses below are warp-collective
-      phase ^= 1u;
+    unsigned char* dA = sA + buf * TC_STAGE_A;
+    unsigned char* dB = sB + buf * TC_STAGE_B;
+    // vector v = (slice, row, k/8): 16 bytes of 8 consecutive k, placed as
+    // K-major 8 x 16-byte core matrices
+    for (int v = tid; v < TC_S * TC_BM * (TC_BK / 8); v += TC_THREADS) {
+      const int sl = v / (TC_BM * (TC_BK / 8)), rem = v % (TC_BM * (TC_BK / 8));
+      const int r = rem / (TC_BK / 8), kq = rem % (TC_BK / 8);
+      cp_async16(dA + sl * TC_SLICE_A_BYTES + ((r >> 3) * (TC_BK / 8) + kq) * 128 + (r & 7) * 16,
+                 Ab + (long long)sl * g.mpad * g.kpad + (long long)(m0 + r) * g.kpad + k0 + kq * 8);
+    }
+    for (int v = tid; v < TC_S * TC_BN * (TC_BK / 8); v += TC_THREADS) {
+      const int sl = v / (TC_BN * (TC_BK / 8)), rem = v % (TC_BN * (TC_BK / 8));
+      const int r = rem / (TC_BK / 8), kq = rem % (TC_BK / 8);
+      cp_async16(dB + sl * TC_SLICE_B_BYTES + ((r >> 3) * (TC_BK / 8) + kq) * 128 + (r & 7) * 16,
+                 Bb + (long long)sl * g.npad * g.kpad + (long long)(n0 + r) * g.kpad + k0 + kq * 8);
+    }
+    asm volatile("cp.async.commit_group;");
+  };
+  uint32_t ph[2] = {0u, 0u};
+  bool pend[2] = {false, false};
+  // wait (bounded, uniform over the CTA) for the MMAs committed on buffer bf
+  auto wait_buf = [&](int bf) {
+    if (!pend[bf]) return;
+    ok = __syncthreads_and(ok && mbar_wait(mbar_addr[bf], ph[bf])) != 0;
+    ph[bf] ^= 1u;
+    pend[bf] = false;
+  };
+  if (Q > 0) load_stage(0, 0);
+  for (int q = 0; q < Q && ok; ++q) {
+    const int buf = q & 1;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // stage q (the only group in flight)
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      ++chunks_since_drain;
-      ++nchunks;
-      const bool last = (k0 + TC_BK >= ke) && (js + 1 == g.nsum);
-      // intermediate drain of the exact groups (the final one is below); every
-      // chunk writes all six accumulators, so a drain is always followed by
-      // fresh MMAs
-      if (ok && !last && chunks_since_drain * TC_BK >= 128) {
+      const uint32_t a0 = smem_u32(sA + buf * TC_STAGE_A), b0 = smem_u32(sB + buf * TC_STAGE_B);
+      for (int s1 = 1; s1 <= TC_S; ++s1)
+        for (int t1 = 1; t1 <= TC_S + 1 - s1; ++t1) {
+          const int gi = s1 + t1;
+          const int a = gi <= 6 ? gi - 2 : 5;
+#pragma unroll
+          for (int ks = 0; ks < TC_BK / 16; ++ks) {
+            const uint64_t ad = smem_desc(a0 + (s1 - 1) * TC_SLICE_A_BYTES + ks * 256, 128, (TC_BK / 8) * 128);
+            const uint64_t bd = smem_desc(b0 + (t1 - 1) * TC_SLICE_B_BYTES + ks * 256, 128, (TC_BK / 8) * 128);
+            const uint32_t accum = (filled >> a) & 1u;
+            mma_bf16(tmem + (uint32_t)(a * TC_BN), ad, bd, IDESC, accum);
+            filled |= (1u << a);
+          }
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          mbar_addr[buf]));
+    }
+    pend[buf] = true;
+    ++chunks_since_drain;
+    ++nchunks;
+    const bool last = q + 1 == Q;
+    if (!last) {  // prefetch stage q + 1 once the MMAs of stage q - 1 released its buffer
+      wait_buf(buf ^ 1);
+      if (ok) load_stage(q + 1, buf ^ 1);
+    }
+    // intermediate drain of the exact groups every 128 k (the final one is
+    // below); every stage writes all six accumulators, so a drain is always
+    // followed by fresh MMAs
+    if (ok && !last && chunks_since_drain * TC_BK >= 128) {
+      wait_buf(buf);  // all MMAs so far complete
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (ok) {
         // |I| grows by < 2^56.1 per drain: every TC_MAX_DRAINS drains the
         // partial sum is written out before it can leave int64 (K > ~15k)
         const bool flush = ++ndrain == TC_MAX_DRAINS;
@@ -322,9 +374,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
         chunks_since_drain = 0;
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();  // TMEM drained / smem free before the next chunk
+      __syncthreads();  // TMEM read before the next MMAs
     }
   }
+  // the last stage's MMAs (and any other pending commit)
+  wait_buf(0);
+  wait_buf(1);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;");
   if (!ok && lane == 0) atomicExch(g.err, 1);
   // ---- final drain + epilogue, 16 columns at a time (row = this thread's
   // TMEM lane): value = (I + 2^32 acc_{g>=7}) 2^(ea + eb - 48), then alpha,
@@ -347,8 +404,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
       for (int j = 0; j < 16; ++j) {
         const int col = cbase + c0 + j;
         if (col < g.n) {
-          const double d = (double)I[j] + (double)(__uint_as_float(r7[j]) * 4294967296.0f);
-          double v = scale_out(d, ea + g.eb[(long long)b * g.npad + col] - 48, g.alpha, aunit, asgn);
+          // (I + 2^32 acc7) 2^(ea + eb - 48): while |I| < 2^55, I 2^8 plus
+          // acc7 rounded at 2^-40 stays exact to 2^-57 of the operands'
+          // row x column maxima; above, acc7 rounded at 2^-32 is below 2^-56
+          // of the result
+          long long J = I[j];
+          int e = ea + g.eb[(long long)b * g.npad + col] - 48;
+          const float a7 = __uint_as_float(r7[j]);
+          const bool fine = J > -(1LL << 55) && J < (1LL << 55);
+          const float t = a7 * (fine ? 0x1p40f : 0x1p32f);
+          const long long add = fabsf(t) < 2147483648.0f ? (long long)__float2int_rn(t) : __float2ll_rn(t);
+          if (fine) {
+            J = J * 256 + add;
+            e -= 8;
+          } else {
+            J += add;
+          }
+          double v = fix_to_double(J, e);
+          if (aunit) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)asgn);
+          else v *= g.alpha;
           const long long ic = row + (long long)col * g.ldc;
           if (flushed) v += C[ic];
           else if (Cin) v = fma(g.beta, Cin[row + (long long)col * g.ldcin], v);
@@ -481,14 +555,14 @@ bool tc_will_handle(const GemmArgs<double>& g) {
   // The tile is 128 x 64 with a 64-wide k chunk: products with a short side
   // (m < 128, n < 64 or k < 64) stay on the FP64 pipe.
   return t_tc.enabled && t_tc.ar && ((t_tc.sites >> g.site) & 1u) && tc_gemm_supported(g) && g.m >= TC_BM &&
-         g.n >= TC_BN && g.k >= TC_BK;
+         g.n >= TC_BN && g.k >= 64;
 }
 
 void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   ProfToken tok = prof_begin(st);  // slicing + tensor-core kernel
   const int mpad = ceil_div(g.m, TC_BM) * TC_BM;
   const int npad = ceil_div(g.n, TC_BN) * TC_BN;
-  const int kpad = ceil_div(g.k, TC_BK) * TC_BK;
+  const int kpad = ceil_div(g.k, TC_KALIGN) * TC_KALIGN;
   const int nsum = std::max(g.nsum, 1);
   const size_t mk = ar.mark();
   // op(A) and op(B)^T the same matrix (a Gram product Y^* Y): one set of
