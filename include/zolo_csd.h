@@ -99,6 +99,31 @@ int csd_polar(csd_ctx* ctx, int dtype, int n,
               void* U1, int ldu1, void* U2, int ldu2, void* V1, int ldv1,
               double* theta, int* rank, csd_info* info);
 
+/* How csd_polar obtains theta (and C = cos theta, S = sin theta):
+ *   mode 0 (default): theta = atan2(S, C) with C, S = diag(V1^* H_i V1)
+ *                     (Algorithm 1 lines 8-9 and remark (iii));
+ *   mode 1:           theta solves sin(theta) - cos(theta) = Lambda, i.e.
+ *                     theta = pi/4 + asin(Lambda / sqrt(2)) (remark (iv)):
+ *                     cheaper (no V1^* H_i V1), still backward stable, and
+ *                     per the paper generally less accurate.
+ * Returns 0, -1 (NULL context) or -2 (other mode). */
+int csd_set_theta_mode(csd_ctx* ctx, int mode);
+
+/* V2 of the complete 2 x 2 CS decomposition (remark (viii)): for a unitary
+ * [A1 A3; A2 A4] (2n x 2n) whose first block column has the full-rank CSD
+ * A1 = U1 C V1^*, A2 = U2 S V1^* (from csd_polar), computes
+ * X = -A3^* U1 S + A4^* U2 C and its QR factorization X = Q R with
+ * diag(R) >= 0, and writes V2 = Q, so that A3 = -U1 S V2^* and
+ * A4 = U2 C V2^* up to the backward error.
+ *   A3, A4   n x n blocks (lda3, lda4 >= n), read only.
+ *   U1, U2   n x n factors from csd_polar (ldu1, ldu2 >= n), read only.
+ *   theta    length n (host or device), C = cos theta, S = sin theta.
+ *   V2       n x n output (ldv2 >= n), unitary.
+ * Returns 0, -k for invalid argument k, or a CSD_ERR_* code. */
+int csd_complete_v2(csd_ctx* ctx, int dtype, int n, const void* A3, int lda3, const void* A4, int lda4,
+                    const void* U1, int ldu1, const void* U2, int ldu2, const double* theta, void* V2, int ldv2,
+                    csd_info* info);
+
 /* Polar decomposition A = W H by Zolo-pd (Section 5) on [eps, 1],
  * eps = 1e-15 (Section 5.1), for an n x n A with ||A||_2 <= 1 (as for the
  * blocks of a partial isometry; larger inputs are scaled by 1/||A||_F first).

@@ -80,8 +80,12 @@ def rank_and_mu(A1, A2):
     return r, (0.0 if r == n else 2.0)
 
 
-def csd(A1, A2, mu=None):
+def csd(A1, A2, mu=None, theta_from="cs"):
     """CS decomposition of the 2n x n partial isometry [A1; A2].
+
+    theta_from = "cs": theta = atan2(S, C) with C, S = diag(V^* H_i V)
+    (lines 8-9, remark (iii)); "lambda": theta solves
+    sin(theta) - cos(theta) = Lambda (remark (iv)).
 
     Returns a dict with theta (ascending, length r), U1, U2 (n x r),
     V1 (n x r), C, S (length r), Lambda (eigenvalues of B, ascending), rank,
@@ -117,9 +121,27 @@ def csd(A1, A2, mu=None):
     # the principal angles lie in [0, pi/2] (Section 1), so rounding below 0
     # or above pi/2 is clamped
     theta = np.clip(np.arctan2(S, C), 0.0, np.pi / 2)
+    if theta_from == "lambda":
+        # sin(t) - cos(t) = sqrt(2) sin(t - pi/4) = Lambda
+        theta = np.clip(np.pi / 4 + np.arcsin(np.clip(lam_r / np.sqrt(2.0), -1.0, 1.0)), 0.0, np.pi / 2)
+    elif theta_from != "cs":
+        raise ValueError("theta_from must be 'cs' or 'lambda'")
     order = np.argsort(theta, kind="stable")
     theta = theta[order]
     U1, U2, V = U1[:, order], U2[:, order], V[:, order]
     return dict(theta=theta, C=np.cos(theta), S=np.sin(theta), U1=U1, U2=U2, V1=V,
                 Lambda=lam, Lambda_r=lam_r[order], rank=V.shape[1], mu=mu,
                 W1=W1, W2=W2, H1=H1, H2=H2, B=B)
+
+
+def complete_v2(A3, A4, U1, U2, theta):
+    """Remark (viii): V2 of the complete 2 x 2 CS decomposition of a unitary
+    [A1 A3; A2 A4], given U1, U2, theta of [A1; A2]:
+    X = -A3^* U1 S + A4^* U2 C, X = Q R with diag(R) >= 0, V2 = Q."""
+    C = np.cos(theta)
+    S = np.sin(theta)
+    X = -_ct(A3) @ (U1 * S[None, :]) + _ct(A4) @ (U2 * C[None, :])
+    Q, R = np.linalg.qr(X)
+    d = np.diag(R)
+    ph = np.where(np.abs(d) > 0, d / np.where(np.abs(d) > 0, np.abs(d), 1.0), 1.0)
+    return Q * ph[None, :]

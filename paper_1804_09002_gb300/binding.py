@@ -80,13 +80,17 @@ def _load():
     lib.zolo_plan.argtypes = [cd, ci, ci, vp, vp]
     lib.csd_profile_enable.argtypes = [vp, ci]
     lib.csd_set_tensor_cores.argtypes = [vp, ci]
+    lib.csd_set_theta_mode.argtypes = [vp, ci]
+    lib.csd_complete_v2.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, vp, ci, vp, vp, ci,
+                                    ctypes.POINTER(csd_info)]
     lib.csd_profile_read.argtypes = [vp, ctypes.POINTER(csd_profile)]
     lib.csd_launch_count.argtypes = []
     lib.csd_launch_count.restype = ctypes.c_longlong
     lib.csd_status_str.argtypes = [ci]
     lib.csd_status_str.restype = ctypes.c_char_p
     for f in ("csd_create", "csd_set_stream", "csd_destroy", "csd_polar", "polar", "heig", "zolo_coeffs",
-              "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc", "csd_set_tensor_cores"):
+              "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc", "csd_set_tensor_cores",
+              "csd_set_theta_mode", "csd_complete_v2"):
         getattr(lib, f).restype = ci
     return lib
 
@@ -95,7 +99,7 @@ lib = _load()
 
 EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes", "csd_polar", "polar", "heig",
             "zolo_coeffs", "zolo_plan", "csd_status_str", "csd_profile_enable", "csd_profile_read",
-            "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores"]
+            "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores", "csd_set_theta_mode", "csd_complete_v2"]
 
 
 class CSDError(RuntimeError):
@@ -228,6 +232,35 @@ class Context:
 
     def workspace_bytes(self):
         return lib.csd_workspace_bytes(self._h)
+
+    def set_theta_mode(self, mode):
+        """0: theta = atan2(S, C) (remark (iii), default); 1: theta from the
+        eigenvalues of B, sin(theta) - cos(theta) = Lambda (remark (iv))."""
+        st = lib.csd_set_theta_mode(self._h, int(mode))
+        if st != 0:
+            raise CSDError(st, "csd_set_theta_mode")
+
+    def complete_v2(self, A3, A4, U1, U2, theta):
+        """V2 of the complete 2 x 2 CSD of a unitary [A1 A3; A2 A4] from the
+        U1, U2, theta of [A1; A2] (remark (viii))."""
+        dt = _dtype_code(A3)
+        A3, p3, l3 = _colmajor(A3)
+        A4, p4, l4 = _colmajor(A4)
+        U1, pu1, lu1 = _colmajor(U1)
+        U2, pu2, lu2 = _colmajor(U2)
+        n = A3.shape[1]
+        if _is_torch(theta):
+            theta = theta.contiguous()
+        else:
+            theta = np.ascontiguousarray(theta, dtype=np.float64)
+        V2 = _empty_like2(A3, n, n)
+        info = csd_info()
+        self._bind_stream(A3)
+        st = lib.csd_complete_v2(self._h, dt, n, p3, l3, p4, l4, pu1, lu1, pu2, lu2, _ptr(theta), _ptr(V2), n,
+                                 ctypes.byref(info))
+        if st != STATUS_OK:
+            raise CSDError(st, "csd_complete_v2")
+        return V2
 
     def csd_polar(self, A1, A2, out=None):
         """CS decomposition of [A1; A2].  Returns dict(U1, U2, V1, theta,

@@ -458,6 +458,16 @@ __global__ void theta_kernel(int n, const double* C, const double* S, double* th
     th[i] = fmin(fmax(atan2(S[i], C[i]), 0.0), 1.5707963267948966);
 }
 
+// remark (iv): theta solves sin(theta) - cos(theta) = Lambda, i.e.
+// sqrt(2) sin(theta - pi/4) = Lambda, theta = pi/4 + asin(Lambda / sqrt(2)),
+// with Lambda / sqrt(2) clamped to [-1, 1] and theta to [0, pi/2].
+__global__ void theta_lambda_kernel(int n, const double* lam, double* th) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double x = fmin(fmax(lam[i] * 0.70710678118654752, -1.0), 1.0);
+    th[i] = fmin(fmax(0.78539816339744831 + asin(x), 0.0), 1.5707963267948966);
+  }
+}
+
 // rank of each key among all keys (ties by index): perm[rank] = index.
 // NaN keys order after +inf, so the ranks always form a permutation.
 __device__ inline double sort_key(double v) { return isnan(v) ? INFINITY : v; }
@@ -578,6 +588,12 @@ void sum_vec(cudaStream_t st, int n, const double* d, double* out) {
 void theta_from_cs(cudaStream_t st, int n, const double* C, const double* S, double* theta) {
   if (n <= 0) return;
   theta_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, C, S, theta);
+  ZCSD_LAUNCH();
+}
+
+void theta_from_lambda(cudaStream_t st, int n, const double* lam, double* theta) {
+  if (n <= 0) return;
+  theta_lambda_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, lam, theta);
   ZCSD_LAUNCH();
 }
 

@@ -106,6 +106,8 @@ void median(cudaStream_t st, int n, const double* d, double* out);
 void sum_vec(cudaStream_t st, int n, const double* d, double* out);
 // theta_j = atan2(S_j, C_j); perm = ascending order of key (ties by index)
 void theta_from_cs(cudaStream_t st, int n, const double* C, const double* S, double* theta);
+// theta = pi/4 + asin(Lambda / sqrt(2)) (remark (iv)), clamped to [0, pi/2]
+void theta_from_lambda(cudaStream_t st, int n, const double* lam, double* theta);
 void sort_perm(cudaStream_t st, int n, const double* key, int* perm);
 // Y[:, j] = X[:, perm[j]] for j < ncols
 template <class T> void gather_cols(cudaStream_t st, int m, int ncols, const T* X, int ldx, const int* perm,

@@ -546,22 +546,26 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     info->eig_offblock = ed.offblock;
   }
   // ---- lines 6-9: C/S = diag(V1^* H_i V1), U_i = W_i V1, theta = atan2(S, C)
+  // (remark (iii)); or theta from Lambda (remark (iv)), which needs no C, S
   T* Vr = V + (long long)lo * n;
   if (rk > 0) {
-    GemmArgs<T> g;  // H_i V1 (into Ut, overwritten by U_i below)
+    GemmArgs<T> g;
     g.batch = 2;
     g.m = n; g.n = rk; g.k = n; g.opA = OP_N; g.opB = OP_N;
-    g.A = H; g.lda = n; g.sA = nn;
+    g.lda = n; g.sA = nn;
     g.B = Vr; g.ldb = n; g.sB = 0;
     g.C = Ut; g.ldc = n; g.sC = nn;
     g.alpha = one; g.beta = zer;
     g.site = GS_ASSEMBLY;
-    gemm(g, st);
     double* Cd = dv;
     double* Sd = dv + n;
     double* th = dv + 2 * n;
-    col_dots<T>(st, n, rk, Vr, n, Ut, n, Cd);
-    col_dots<T>(st, n, rk, Vr, n, Ut + nn, n, Sd);
+    if (cx.theta_mode == 0) {
+      g.A = H;  // H_i V1 (into Ut, overwritten by U_i below)
+      gemm(g, st);
+      col_dots<T>(st, n, rk, Vr, n, Ut, n, Cd);
+      col_dots<T>(st, n, rk, Vr, n, Ut + nn, n, Sd);
+    }
     g.A = W;  // U_i = W_i V1
     gemm(g, st);
     if (mu != 0.0) {
@@ -595,7 +599,8 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
         gemm(gi, st);
       }
     }
-    theta_from_cs(st, rk, Cd, Sd, th);
+    if (cx.theta_mode == 0) theta_from_cs(st, rk, Cd, Sd, th);
+    else theta_from_lambda(st, rk, lam + lo, th);
     sort_perm(st, rk, th, perm);
     gather_vec(st, rk, th, perm, theta);
     gather_cols<T>(st, n, rk, Ut, n, perm, U1, ldu1);
@@ -610,6 +615,54 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
   if (rank_out) *rank_out = rk;
   if (info) info->rank = rk;
   return status;
+}
+
+// Remark (viii): V2 of the complete 2 x 2 CS decomposition of a unitary
+// [A1 A3; A2 A4], given U1, U2, theta of [A1; A2]: X = -A3^* U1 S + A4^* U2 C,
+// X = Q R with diag(R) >= 0, V2 = Q.
+template <class T>
+__global__ void scale_cs_kernel(int n, const T* U1, int ldu1, const T* U2, int ldu2, const double* theta, T* P) {
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    P[t] = scal(sin(theta[j]), U1[i + (long long)j * ldu1]);       // U1 S
+    P[nn + t] = scal(cos(theta[j]), U2[i + (long long)j * ldu2]);  // U2 C
+  }
+}
+
+template <class T>
+__global__ void scale_cols_kernel(int n, const T* Q, const T* d, T* V, int ldv) {
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    V[i + (long long)j * ldv] = mul(Q[t], d[j]);
+  }
+}
+
+template <class T>
+int complete_v2_impl(Ctx& cx, Arena& ar, int n, const T* A3, int lda3, const T* A4, int lda4, const T* U1, int ldu1,
+                     const T* U2, int ldu2, const double* theta, T* V2, int ldv2) {
+  cudaStream_t st = cx.stream;
+  const long long nn = (long long)n * n;
+  T* P = ar.get<T>(2 * nn);
+  T* X = ar.get<T>(nn);
+  T* Q = ar.get<T>(nn);
+  T* d = ar.get<T>(n);
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
+  scale_cs_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, U1, ldu1, U2, ldu2, theta, P);
+  ZCSD_LAUNCH();
+  gemm1<T>(st, OP_C, OP_N, n, n, n, mone, A3, lda3, P, n, zer, X, n, 0, 0, GS_OTHER);      // -A3^* U1 S
+  gemm1<T>(st, OP_C, OP_N, n, n, n, one, A4, lda4, P + nn, n, one, X, n, 0, 0, GS_OTHER);  // + A4^* U2 C
+  const size_t mq = ar.mark();
+  QRStore<T> q = qr_alloc<T>(ar, n, n, n, 1);
+  qr_factor<T>(st, ar, q, X, n, 0);
+  qr_form_q<T>(st, ar, q, Q, n, 0);
+  ar.release(mq);
+  diag_phase_kernel<T><<<ceil_div(n, 256), 256, 0, st>>>(n, X, n, d);
+  ZCSD_LAUNCH();
+  scale_cols_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, Q, d, V2, ldv2);
+  ZCSD_LAUNCH();
+  return CSD_OK;
 }
 
 template <class T>
@@ -917,6 +970,25 @@ int heig_typed(csd_ctx* ctx, int n, const void* B, int ldb, double* lam, void* V
   });
 }
 
+template <class T>
+int complete_v2_typed(csd_ctx* ctx, int n, const void* A3, int lda3, const void* A4, int lda4, const void* U1,
+                      int ldu1, const void* U2, int ldu2, const double* theta, void* V2, int ldv2, csd_info* info) {
+  Ctx& cx = ctx->cx;
+  const size_t need = heig_bytes(n, sizeof(T)) + (size_t)8 * n * n * sizeof(T);
+  return run_with_ws(cx, need, info, [&](Arena& ar) -> int {
+    Mat<T> a3 = view_in<T>(cx, ar, A3, lda3, n, n);
+    Mat<T> a4 = view_in<T>(cx, ar, A4, lda4, n, n);
+    Mat<T> u1 = view_in<T>(cx, ar, U1, ldu1, n, n);
+    Mat<T> u2 = view_in<T>(cx, ar, U2, ldu2, n, n);
+    Mat<double> th = view_in<double>(cx, ar, theta, n, n, 1);
+    Mat<T> v2 = view_out<T>(ar, V2, ldv2, n, n);
+    int st = complete_v2_impl<T>(cx, ar, n, a3.d, a3.ld, a4.d, a4.ld, u1.d, u1.ld, u2.d, u2.ld, th.d, v2.d, v2.ld);
+    if (st == CSD_OK) copy_out(cx, v2, n, n);
+    ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+    return st;
+  });
+}
+
 }  // namespace
 
 extern "C" {
@@ -968,11 +1040,7 @@ long long csd_launch_count(void) { return launch_count(); }
 int csd_set_tensor_cores(csd_ctx* ctx, int enable) {
   if (!ctx) return -1;
   ctx->cx.tensor_cores = enable != 0;
-  // -1: every site whose products stay FP64-accurate when sliced.  The
-  // trailing update C -= Y W2 of the stacked [X; sqrt(c) I] factorization is
-  // excluded: it needs the componentwise accuracy of the FP64 pipe (sliced
-  // products are accurate relative to row / column maxima only).
-  ctx->cx.tc_sites = (unsigned)enable;  // -1: every site
+  ctx->cx.tc_sites = (unsigned)enable;  // bit s: call site s; -1: every site
   return CSD_OK;
 }
 
@@ -1031,6 +1099,36 @@ int csd_polar(csd_ctx* ctx, int dtype, int n, const void* A1, int lda1, const vo
   if (dtype == CSD_F64)
     return csd_typed<double>(ctx, n, A1, lda1, A2, lda2, U1, ldu1, U2, ldu2, V1, ldv1, theta, rank, info);
   return csd_typed<z64>(ctx, n, A1, lda1, A2, lda2, U1, ldu1, U2, ldu2, V1, ldv1, theta, rank, info);
+}
+
+int csd_complete_v2(csd_ctx* ctx, int dtype, int n, const void* A3, int lda3, const void* A4, int lda4,
+                    const void* U1, int ldu1, const void* U2, int ldu2, const double* theta, void* V2, int ldv2,
+                    csd_info* info) {
+  if (!ctx) return -1;
+  if (dtype != CSD_F64 && dtype != CSD_C128) return -2;
+  if (n < 1) return -3;
+  if (!A3) return -4;
+  if (lda3 < n) return -5;
+  if (!A4) return -6;
+  if (lda4 < n) return -7;
+  if (!U1) return -8;
+  if (ldu1 < n) return -9;
+  if (!U2) return -10;
+  if (ldu2 < n) return -11;
+  if (!theta) return -12;
+  if (!V2) return -13;
+  if (ldv2 < n) return -14;
+  if (info) std::memset(info, 0, sizeof(csd_info));
+  if (dtype == CSD_F64)
+    return complete_v2_typed<double>(ctx, n, A3, lda3, A4, lda4, U1, ldu1, U2, ldu2, theta, V2, ldv2, info);
+  return complete_v2_typed<z64>(ctx, n, A3, lda3, A4, lda4, U1, ldu1, U2, ldu2, theta, V2, ldv2, info);
+}
+
+int csd_set_theta_mode(csd_ctx* ctx, int mode) {
+  if (!ctx) return -1;
+  if (mode != 0 && mode != 1) return -2;
+  ctx->cx.theta_mode = mode;
+  return CSD_OK;
 }
 
 int polar(csd_ctx* ctx, int dtype, int n, const void* A, int lda, void* W, int ldw, void* H, int ldh,

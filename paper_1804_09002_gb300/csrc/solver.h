@@ -30,6 +30,7 @@ struct Ctx {
   Profiler prof;
   bool tensor_cores = false;
   unsigned tc_sites = 0;
+  int theta_mode = 0;  // 0: atan2(S, C) (remark (iii)); 1: from Lambda (remark (iv))
 };
 
 struct PolarDiag {

@@ -318,3 +318,63 @@ def test_csd_rank_deficient_kept_zero_sine(B):
     assert R["info"]["mu"] == 2.0 and R["info"]["alg2_used"][1] == 1
     ref = O.csd(A1, A2)
     _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=k)
+
+
+# ------------------------------------------------ remarks (iv) and (viii)
+@pytest.mark.parametrize("case", ["haar", "rankdef"])
+def test_csd_theta_from_lambda(B, case):
+    """Remark (iv): theta from sin(theta) - cos(theta) = Lambda (context mode
+    1) against the oracle's same reading, plus the CSD bars."""
+    if case == "haar":
+        n, k = 100, 100
+        A1, A2, th = I.haar_csd(n, seed=73)
+    else:
+        n, k = 64, 48
+        A1, A2, th = I.rankdef_csd(n, k, seed=74, cplx=False, n_repeat=8)
+    ctx = B.Context(0)
+    try:
+        ctx.set_theta_mode(1)
+        R = ctx.csd_polar(to_dev(A1), to_dev(A2))
+    finally:
+        ctx.close()
+    ref = O.csd(A1, A2, theta_from="lambda")
+    _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=k)
+    assert np.max(np.abs(to_host(R["theta"])[:k] - th)) <= 1e-12 * n
+
+
+@pytest.mark.parametrize("n,cplx", [(64, False), (130, False), (40, True)])
+def test_complete_v2(B, n, cplx):
+    """Remark (viii): V2 of the complete 2 x 2 CSD of a unitary 2n x 2n.
+    (a) From the oracle's U1, U2, theta, the GPU V2 equals the oracle's
+    (X is unitary up to O(u), so its QR with diag(R) >= 0 is well
+    conditioned); (b) from the GPU's own csd_polar outputs,
+    A3 = -U1 S V2^* and A4 = U2 C V2^* to 50 n u, V2 unitary."""
+    rng = np.random.default_rng(90 + n)
+    Q = I.haar(2 * n, rng, cplx)
+    A1, A2, A3, A4 = Q[:n, :n], Q[n:, :n], Q[:n, n:], Q[n:, n:]
+    ref = O.csd(A1, A2)
+    V2o = O.complete_v2(A3, A4, ref["U1"], ref["U2"], ref["theta"])
+    V2 = to_host(B.default_context(0).complete_v2(to_dev(A3), to_dev(A4), to_dev(ref["U1"]), to_dev(ref["U2"]),
+                                                  torch.from_numpy(ref["theta"]).cuda()))
+    assert np.max(np.abs(V2 - V2o)) <= 1e-12 * n
+    R = B.csd_polar(to_dev(A1), to_dev(A2))
+    U1, U2, th = to_host(R["U1"]), to_host(R["U2"]), to_host(R["theta"])
+    V2g = to_host(B.default_context(0).complete_v2(to_dev(A3), to_dev(A4), R["U1"], R["U2"], R["theta"]))
+    C, S = np.cos(th), np.sin(th)
+    r3 = np.linalg.norm(A3 + (U1 * S[None, :]) @ V2g.conj().T) / np.sqrt(n)
+    r4 = np.linalg.norm(A4 - (U2 * C[None, :]) @ V2g.conj().T) / np.sqrt(n)
+    assert max(r3, r4) <= 50 * n * U
+    assert M.orthogonality(V2g) <= 50 * n * U
+
+
+def test_complete_v2_host_pointers(B):
+    n = 33
+    rng = np.random.default_rng(95)
+    Q = I.haar(2 * n, rng, False)
+    A1, A2, A3, A4 = Q[:n, :n], Q[n:, :n], Q[:n, n:], Q[n:, n:]
+    ref = O.csd(A1, A2)
+    V2o = O.complete_v2(A3, A4, ref["U1"], ref["U2"], ref["theta"])
+    V2 = B.default_context(0).complete_v2(np.asfortranarray(A3), np.asfortranarray(A4), ref["U1"], ref["U2"],
+                                          ref["theta"])
+    assert isinstance(V2, np.ndarray)
+    assert np.max(np.abs(V2 - V2o)) <= 1e-12 * n

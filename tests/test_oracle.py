@@ -255,3 +255,51 @@ def test_planted_missing_shift_is_caught(monkeypatch):
     A1, A2, th = I.rankdef_csd(24, 18, seed=23, cplx=False, n_repeat=2)
     R = O.csd(A1, A2, mu=0.0)
     assert R["V1"].shape[1] != 18
+
+
+# ------------------------------------------------ remarks (iv) and (viii)
+@pytest.mark.parametrize("n,cplx", [(40, False), (24, True)])
+def test_theta_from_lambda_remark_iv(n, cplx):
+    """theta from sin(theta) - cos(theta) = Lambda: the known angles within
+    O(u) (d theta / d Lambda = 1 / (cos + sin) <= 1 on [0, pi/2]), the
+    defining equation on the kept eigenvalues, and a backward-stable CSD."""
+    A1, A2, th = I.haar_csd(n, seed=70 + n, cplx=cplx)
+    R = O.csd(A1, A2, theta_from="lambda")
+    assert np.max(np.abs(R["theta"] - th)) <= 1e-12 * n
+    lam = np.sort(R["Lambda_r"])
+    assert np.max(np.abs(np.sin(R["theta"]) - np.cos(R["theta"]) - lam)) <= 1e-14 * n
+    be = M.backward_error_fro(A1, A2, R["U1"], R["U2"], R["theta"], R["V1"])
+    assert be <= 50 * n * u
+
+
+def test_theta_from_lambda_rank_deficient():
+    n, k = 32, 24
+    A1, A2, th = I.rankdef_csd(n, k, seed=71, cplx=False, n_repeat=4)
+    R = O.csd(A1, A2, theta_from="lambda")
+    assert R["rank"] == k
+    assert np.max(np.abs(R["theta"] - th)) <= 1e-12 * n
+
+
+def _complete_blocks(n, cplx, seed):
+    rng = np.random.default_rng(seed)
+    Q = I.haar(2 * n, rng, cplx)
+    return Q[:n, :n], Q[n:, :n], Q[:n, n:], Q[n:, n:]
+
+
+@pytest.mark.parametrize("n,cplx", [(24, False), (16, True)])
+def test_complete_2x2_csd_remark_viii(n, cplx):
+    """For a unitary [A1 A3; A2 A4], V2 from X = -A3^* U1 S + A4^* U2 C
+    completes the 2 x 2 CSD: A3 = -U1 S V2^*, A4 = U2 C V2^*, V2 unitary
+    (the defining identities of remark (viii), checked to O(u))."""
+    A1, A2, A3, A4 = _complete_blocks(n, cplx, 80 + n)
+    R = O.csd(A1, A2)
+    V2 = O.complete_v2(A3, A4, R["U1"], R["U2"], R["theta"])
+    C, S = np.cos(R["theta"]), np.sin(R["theta"])
+    r3 = np.linalg.norm(A3 + (R["U1"] * S[None, :]) @ V2.conj().T)
+    r4 = np.linalg.norm(A4 - (R["U2"] * C[None, :]) @ V2.conj().T)
+    assert max(r3, r4) <= 50 * n * u
+    assert M.orthogonality(V2) <= 10 * n * u
+    # a sign slip in X (+A3 instead of -A3) breaks the identity
+    X = (A3.conj().T @ (R["U1"] * S[None, :])) + A4.conj().T @ (R["U2"] * C[None, :])
+    Qw = np.linalg.qr(X)[0]
+    assert np.linalg.norm(A3 + (R["U1"] * S[None, :]) @ Qw.conj().T) > 1e-3
