@@ -27,6 +27,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_CSD = lambda n: 198.0 * n ** 3
+WORKLOAD = lambda n: (f"real FP64 CSD n={n}, clustered theta (1/2 uniform, 1/4 within 1e-8 of 0, "
+                      f"1/4 within 1e-8 of pi/2), 1e-14 noise, re-orthonormalised")
 U = 2.0 ** -53
 
 
@@ -159,8 +161,9 @@ def run_reference(args, rank, ws):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "tflops": FLOPS_PER_CSD(args.n) / t / 1e12,
-        "config": {"workload": f"real FP64 CSD n={args.n}, clustered theta, 1e-14 noise, re-orthonormalised",
-                   "n": args.n, "l2": "inputs larger than L2"},
+        "config": {"workload": WORKLOAD(args.n), "n": args.n, "parallelism": "replicas x1",
+                   "l2": "inputs larger than L2 (2 x 128 MiB)",
+                   "products": "CPU oracle (one-sided Jacobi SVD polar, cyclic Jacobi eig), FP64"},
         "cpu_baseline": {"value": t, "unit": "s/CSD", "cores": OJ.threads(), "kind": "oracle",
                          "sample": f"oracle CSD of an n={ns} instance of the same recipe, median of {args.steps}, "
                                    f"scaled by (n/{ns})^3"},
@@ -330,8 +333,7 @@ def main():
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "tflops": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12,
         "tflops_frac_of_fp64_peak": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12 / fp64_alu_peak_tflops(),
-        "config": {"workload": f"real FP64 CSD n={n}, clustered theta (1/2 uniform, 1/4 within 1e-8 of 0, "
-                               f"1/4 within 1e-8 of pi/2), 1e-14 noise, re-orthonormalised",
+        "config": {"workload": WORKLOAD(n),
                    "n": n, "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (2 x 128 MiB)",
                    "products": products},
         "accuracy": acc,
