@@ -8,7 +8,7 @@ remark (iii), written out step by step in FP64 with *independent* sub-solvers:
     (A V = U Sigma, W = U V^*, H = V Sigma V^*; Section 1, eqs. for A1/A2),
   * Hermitian eigendecomposition of B by cyclic Jacobi.
 
-Readings taken where the paper leaves a choice (listed in the design doc):
+Readings taken where the paper leaves a choice:
   * rank r = round(||A||_F^2) and mu = 0 if r = n else 2 (remark (vi), line 3);
   * H_i symmetrised as (H + H^*)/2 (Theorem 3.1 assumes H Hermitian);
   * theta = atan2(S, C) (remark (iii), arctan(S/C) read with quadrant),
