@@ -749,7 +749,7 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Upper bound of the workspace (bytes) needed by a call; the driver also
+// Upper bound of the workspace (bytes) needed by a call; run_with_ws also
 // grows the arena and retries if a bound turns out short.
 size_t polar_bytes(long long n, int P, size_t es) {
   const long long nn = n * n;
