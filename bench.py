@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sample-n", type=int, default=512, help="oracle sample size for the CPU baseline")
+    ap.add_argument("--sample-n", type=int, default=1024,
+                    help="oracle sample size for the CPU baseline (about 20 s on 16 Grace cores)")
     ap.add_argument("--tc", type=int, default=1,
                     help="1 (default): real FP64 products on the tcgen05 tensor cores (exact BF16 slicing); 0: FP64 pipe")
     ap.add_argument("--compare-fp64", type=int, default=1,
