@@ -9,7 +9,9 @@
  * Zolo-eig (Section 5), and U_i = W_i V1, C/S = diag(V1^* H_i V1),
  * theta = atan2(S, C) (Algorithm 1 lines 6-9, remark (iii)).  Ill-conditioned
  * blocks use the eps-modified Zolo-pd with eps = 1e-15 and, when W_i is not
- * orthonormal, Algorithm 2; rank-deficient inputs use Algorithm 3.
+ * orthonormal, Algorithm 2; rank-deficient inputs use Algorithm 3, with
+ * Algorithm 2's W_i for a block whose U_i = W_i V1 is not orthonormal (C or S
+ * ill conditioned, Section 5.2).
  *
  * Conventions for every entry point
  *   - Matrices are column-major with leading dimension ld >= n.
