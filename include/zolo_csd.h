@@ -101,6 +101,18 @@ int csd_polar(csd_ctx* ctx, int dtype, int n,
               void* U1, int ldu1, void* U2, int ldu2, void* V1, int ldv1,
               double* theta, int* rank, csd_info* info);
 
+/* CS decomposition with rectangular blocks: A1 is m1 x n, A2 is m2 x n,
+ * m1, m2 >= n (a 2-block partial isometry, Section 2).  Each block is first
+ * reduced by its Householder QR, A_i = Q_i R_i; [R1; R2] has orthonormal
+ * columns (or is the same partial isometry) and goes through csd_polar's
+ * path; U_i = Q_i U_i'.
+ *   U1 (m1 x n, ldu1 >= m1), U2 (m2 x n, ldu2 >= m2): columns 0..rank-1
+ *   hold the factors; V1 (n x n), theta (length n) and rank as in csd_polar.
+ * Returns as csd_polar; -3 / -4 when m1 / m2 < n, -5 when n < 1. */
+int csd_polar_rect(csd_ctx* ctx, int dtype, int m1, int m2, int n, const void* A1, int lda1, const void* A2,
+                   int lda2, void* U1, int ldu1, void* U2, int ldu2, void* V1, int ldv1, double* theta, int* rank,
+                   csd_info* info);
+
 /* How csd_polar obtains theta (and C = cos theta, S = sin theta):
  *   mode 0 (default): theta = atan2(S, C) with C, S = diag(V1^* H_i V1)
  *                     (Algorithm 1 lines 8-9 and remark (iii));

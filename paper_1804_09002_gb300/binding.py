@@ -81,6 +81,8 @@ def _load():
     lib.csd_profile_enable.argtypes = [vp, ci]
     lib.csd_set_tensor_cores.argtypes = [vp, ci]
     lib.csd_set_theta_mode.argtypes = [vp, ci]
+    lib.csd_polar_rect.argtypes = [vp, ci, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp, ci, vp, ci, vp,
+                                   ctypes.POINTER(ci), ctypes.POINTER(csd_info)]
     lib.csd_complete_v2.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, vp, ci, vp, vp, ci,
                                     ctypes.POINTER(csd_info)]
     lib.csd_profile_read.argtypes = [vp, ctypes.POINTER(csd_profile)]
@@ -90,7 +92,7 @@ def _load():
     lib.csd_status_str.restype = ctypes.c_char_p
     for f in ("csd_create", "csd_set_stream", "csd_destroy", "csd_polar", "polar", "heig", "zolo_coeffs",
               "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc", "csd_set_tensor_cores",
-              "csd_set_theta_mode", "csd_complete_v2"):
+              "csd_set_theta_mode", "csd_complete_v2", "csd_polar_rect"):
         getattr(lib, f).restype = ci
     return lib
 
@@ -99,7 +101,8 @@ lib = _load()
 
 EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes", "csd_polar", "polar", "heig",
             "zolo_coeffs", "zolo_plan", "csd_status_str", "csd_profile_enable", "csd_profile_read",
-            "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores", "csd_set_theta_mode", "csd_complete_v2"]
+            "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores", "csd_set_theta_mode", "csd_complete_v2",
+            "csd_polar_rect"]
 
 
 class CSDError(RuntimeError):
@@ -287,6 +290,31 @@ class Context:
                            ctypes.byref(rank), ctypes.byref(info))
         if st not in (STATUS_OK, WARN_ALG2_RCHECK):
             raise CSDError(st, "csd_polar")
+        return dict(U1=U1, U2=U2, V1=V1, theta=theta, rank=rank.value, info=info.as_dict(), status=st)
+
+    def csd_polar_rect(self, A1, A2):
+        """CS decomposition of [A1; A2] with A1 m1 x n, A2 m2 x n (m_i >= n).
+        Returns dict(U1 (m1 x n), U2 (m2 x n), V1, theta, rank, info)."""
+        dt = _dtype_code(A1)
+        if _dtype_code(A2) != dt:
+            raise TypeError("A1 and A2 must share a dtype")
+        A1, p1, l1 = _colmajor(A1)
+        A2, p2, l2 = _colmajor(A2)
+        m1, n = A1.shape
+        m2 = A2.shape[0]
+        if A2.shape[1] != n:
+            raise ValueError("A1 and A2 must have the same number of columns")
+        U1 = _empty_like2(A1, m1, n)
+        U2 = _empty_like2(A1, m2, n)
+        V1 = _empty_like2(A1, n, n)
+        theta = _empty_vec(A1, n)
+        rank = ctypes.c_int()
+        info = csd_info()
+        self._bind_stream(A1)
+        st = lib.csd_polar_rect(self._h, dt, m1, m2, n, p1, l1, p2, l2, _ptr(U1), m1, _ptr(U2), m2, _ptr(V1), n,
+                                _ptr(theta), ctypes.byref(rank), ctypes.byref(info))
+        if st not in (STATUS_OK, WARN_ALG2_RCHECK):
+            raise CSDError(st, "csd_polar_rect")
         return dict(U1=U1, U2=U2, V1=V1, theta=theta, rank=rank.value, info=info.as_dict(), status=st)
 
     def polar(self, A, want_h=True):

@@ -665,6 +665,56 @@ int complete_v2_impl(Ctx& cx, Arena& ar, int n, const T* A3, int lda3, const T* 
   return CSD_OK;
 }
 
+// Rectangular blocks A_i (m_i x n, m_i >= n; the partial isometries of
+// Section 2): A_i = Q_i R_i by Householder QR (Q_i with orthonormal columns),
+// the square CSD of [R1; R2] (its columns are orthonormal as well, since
+// R1^* R1 + R2^* R2 = A^* A), and U_i = Q_i U_i'.
+template <class T>
+__global__ void upper_tri_kernel(int n, const T* M, int ldm, T* R) {
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    R[t] = (i <= j) ? M[i + (long long)j * ldm] : zero<T>();
+  }
+}
+
+template <class T>
+int csd_rect_impl(Ctx& cx, Arena& ar, int m1, int m2, int n, const T* A1, int lda1, const T* A2, int lda2, T* U1,
+                  int ldu1, T* U2, int ldu2, T* V1, int ldv1, double* theta, int* rank_out, csd_info* info) {
+  cudaStream_t st = cx.stream;
+  const long long nn = (long long)n * n;
+  T* R = ar.get<T>(2 * nn);  // R1 | R2, n x n each
+  T* Q1 = ar.get<T>((size_t)m1 * n);
+  T* Q2 = ar.get<T>((size_t)m2 * n);
+  T* Us = ar.get<T>(2 * nn);  // U1', U2' of the square CSD
+  const T one = from_re<T>(1.0), zer = zero<T>();
+  for (int i = 0; i < 2; ++i) {
+    const int m = i == 0 ? m1 : m2;
+    const T* A = i == 0 ? A1 : A2;
+    const int lda = i == 0 ? lda1 : lda2;
+    T* Q = i == 0 ? Q1 : Q2;
+    const size_t mk = ar.mark();
+    T* M = ar.get<T>((size_t)m * n);
+    axpby<T>(st, m, n, 1.0, A, lda, 0, 0.0, M, m, 0, 1);
+    QRStore<T> q = qr_alloc<T>(ar, m, n, m, 1);
+    qr_factor<T>(st, ar, q, M, m, 0);
+    qr_form_q<T>(st, ar, q, Q, m, 0);
+    upper_tri_kernel<T><<<grid_for(nn), 256, 0, st>>>(n, M, m, R + i * nn);
+    ZCSD_LAUNCH();
+    ar.release(mk);
+  }
+  int rk = 0;
+  const int stt = csd_impl<T>(cx, ar, n, R, n, R + nn, n, Us, n, Us + nn, n, V1, ldv1, theta, &rk, info);
+  if (stt != CSD_OK && stt != CSD_WARN_ALG2_RCHECK) return stt;
+  if (rk > 0) {
+    gemm1<T>(st, OP_N, OP_N, m1, rk, n, one, Q1, m1, Us, n, zer, U1, ldu1, 0, 0, GS_ASSEMBLY);
+    gemm1<T>(st, OP_N, OP_N, m2, rk, n, one, Q2, m2, Us + nn, n, zer, U2, ldu2, 0, 0, GS_ASSEMBLY);
+  }
+  ZCSD_CUDA(cudaStreamSynchronize(st));
+  if (rank_out) *rank_out = rk;
+  return stt;
+}
+
 template <class T>
 int polar_impl(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* Wo, int ldw, T* Ho, int ldh, csd_info* info) {
   cudaStream_t st = cx.stream;
@@ -971,6 +1021,34 @@ int heig_typed(csd_ctx* ctx, int n, const void* B, int ldb, double* lam, void* V
 }
 
 template <class T>
+int csd_rect_typed(csd_ctx* ctx, int m1, int m2, int n, const void* A1, int lda1, const void* A2, int lda2, void* U1,
+                   int ldu1, void* U2, int ldu2, void* V1, int ldv1, double* theta, int* rank, csd_info* info) {
+  Ctx& cx = ctx->cx;
+  const size_t need = csd_bytes(n, sizeof(T)) + (size_t)(4 * (long long)(m1 + m2) * n + 8LL * n * n) * sizeof(T) +
+                      heig_bytes(std::max(m1, m2), sizeof(T)) / 4;
+  return run_with_ws(cx, need, info, [&](Arena& ar) -> int {
+    Mat<T> a1 = view_in<T>(cx, ar, A1, lda1, m1, n);
+    Mat<T> a2 = view_in<T>(cx, ar, A2, lda2, m2, n);
+    Mat<T> u1 = view_out<T>(ar, U1, ldu1, m1, n);
+    Mat<T> u2 = view_out<T>(ar, U2, ldu2, m2, n);
+    Mat<T> v1 = view_out<T>(ar, V1, ldv1, n, n);
+    Mat<double> th = view_out<double>(ar, theta, n, n, 1);
+    int rk = 0;
+    int st = csd_rect_impl<T>(cx, ar, m1, m2, n, a1.d, a1.ld, a2.d, a2.ld, u1.d, u1.ld, u2.d, u2.ld, v1.d, v1.ld, th.d,
+                              &rk, info);
+    if (st == CSD_OK || st == CSD_WARN_ALG2_RCHECK) {
+      copy_out(cx, u1, m1, n);
+      copy_out(cx, u2, m2, n);
+      copy_out(cx, v1, n, n);
+      copy_out(cx, th, n, 1);
+      ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+      if (rank) *rank = rk;
+    }
+    return st;
+  });
+}
+
+template <class T>
 int complete_v2_typed(csd_ctx* ctx, int n, const void* A3, int lda3, const void* A4, int lda4, const void* U1,
                       int ldu1, const void* U2, int ldu2, const double* theta, void* V2, int ldv2, csd_info* info) {
   Ctx& cx = ctx->cx;
@@ -1099,6 +1177,32 @@ int csd_polar(csd_ctx* ctx, int dtype, int n, const void* A1, int lda1, const vo
   if (dtype == CSD_F64)
     return csd_typed<double>(ctx, n, A1, lda1, A2, lda2, U1, ldu1, U2, ldu2, V1, ldv1, theta, rank, info);
   return csd_typed<z64>(ctx, n, A1, lda1, A2, lda2, U1, ldu1, U2, ldu2, V1, ldv1, theta, rank, info);
+}
+
+int csd_polar_rect(csd_ctx* ctx, int dtype, int m1, int m2, int n, const void* A1, int lda1, const void* A2,
+                   int lda2, void* U1, int ldu1, void* U2, int ldu2, void* V1, int ldv1, double* theta, int* rank,
+                   csd_info* info) {
+  if (!ctx) return -1;
+  if (dtype != CSD_F64 && dtype != CSD_C128) return -2;
+  if (n < 1) return -5;
+  if (m1 < n) return -3;
+  if (m2 < n) return -4;
+  if (!A1) return -6;
+  if (lda1 < m1) return -7;
+  if (!A2) return -8;
+  if (lda2 < m2) return -9;
+  if (!U1) return -10;
+  if (ldu1 < m1) return -11;
+  if (!U2) return -12;
+  if (ldu2 < m2) return -13;
+  if (!V1) return -14;
+  if (ldv1 < n) return -15;
+  if (!theta) return -16;
+  if (info) std::memset(info, 0, sizeof(csd_info));
+  if (dtype == CSD_F64)
+    return csd_rect_typed<double>(ctx, m1, m2, n, A1, lda1, A2, lda2, U1, ldu1, U2, ldu2, V1, ldv1, theta, rank,
+                                  info);
+  return csd_rect_typed<z64>(ctx, m1, m2, n, A1, lda1, A2, lda2, U1, ldu1, U2, ldu2, V1, ldv1, theta, rank, info);
 }
 
 int csd_complete_v2(csd_ctx* ctx, int dtype, int n, const void* A3, int lda3, const void* A4, int lda4,

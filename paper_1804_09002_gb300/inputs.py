@@ -77,6 +77,27 @@ def _reorthonormalise(A1, A2):
     return np.asfortranarray(Q[:n]), np.asfortranarray(Q[n:])
 
 
+def rect_csd(m1, m2, n, seed=6, cplx=False, k=None):
+    """Partial isometry with rectangular blocks A_i (m_i x n, m_i >= n):
+    A1 = U1[:, :n] diag(cos theta) V^*, A2 = U2[:, :n] diag(sin theta) V^*
+    with Haar U1 (m1 x m1), U2 (m2 x m2), V; theta i.i.d. U[0, pi/2]; with k
+    given, n - k indices get C = S = 0.  Returns (A1, A2, theta_sorted of the
+    kept indices)."""
+    rng = _rng(seed)
+    theta = rng.uniform(0.0, HALF_PI, n)
+    mask = np.ones(n, bool)
+    if k is not None:
+        mask[rng.permutation(n)[: n - k]] = False
+    U1 = haar(m1, rng, cplx)
+    U2 = haar(m2, rng, cplx)
+    V = haar(n, rng, cplx)
+    c = np.where(mask, np.cos(theta), 0.0)
+    s = np.where(mask, np.sin(theta), 0.0)
+    A1 = (U1[:, :n] * c[None, :]) @ V.conj().T
+    A2 = (U2[:, :n] * s[None, :]) @ V.conj().T
+    return np.asfortranarray(A1), np.asfortranarray(A2), np.sort(theta[mask])
+
+
 def haar_csd(n, seed=1, cplx=False):
     """theta i.i.d. U[0, pi/2]; returns (A1, A2, theta_sorted)."""
     rng = _rng(seed)

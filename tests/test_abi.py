@@ -46,6 +46,7 @@ def test_bad_arguments_are_rejected_without_a_device(B):
     assert lib.csd_destroy(None) == 0
     assert lib.csd_complete_v2(None, 0, 4, None, 4, None, 4, None, 4, None, 4, None, None, 4, None) == -1
     assert lib.csd_set_theta_mode(None, 1) == -1
+    assert lib.csd_polar_rect(None, 0, 8, 8, 4, None, 8, None, 8, None, 8, None, 8, None, 4, None, None, None) == -1
     assert lib.zolo_coeffs(0.0, 8, None, None, None, None) == -1
     assert lib.zolo_coeffs(0.5, 0, None, None, None, None) == -2
     assert B.lib.csd_status_str(-3) == b"invalid argument"

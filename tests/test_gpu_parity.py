@@ -378,3 +378,26 @@ def test_complete_v2_host_pointers(B):
                                           ref["theta"])
     assert isinstance(V2, np.ndarray)
     assert np.max(np.abs(V2 - V2o)) <= 1e-12 * n
+
+
+@pytest.mark.parametrize("m1,m2,n,cplx,k", [(80, 70, 48, False, None), (130, 100, 100, False, None),
+                                           (60, 50, 40, True, None), (72, 64, 48, False, 36)])
+def test_csd_rectangular(B, m1, m2, n, cplx, k):
+    """Rectangular blocks (csd_polar_rect): QR of each block, square CSD of
+    [R1; R2], U_i = Q_i U_i'; against the oracle, which takes the
+    rectangular polar decompositions directly."""
+    A1, A2, th = I.rect_csd(m1, m2, n, seed=m1 + n, cplx=cplx, k=k)
+    R = B.default_context(0).csd_polar_rect(to_dev(A1), to_dev(A2))
+    ref = O.csd(A1, A2)
+    r = ref["rank"]
+    assert R["rank"] == r
+    got = to_host(R["theta"])[:r]
+    assert np.all(np.diff(got) >= 0) and np.all(got >= 0) and np.all(got <= np.pi / 2 + 1e-15)
+    assert np.max(np.abs(got - ref["theta"])) <= 1e-12 * n
+    assert np.max(np.abs(got - th)) <= 1e-12 * n
+    U1, U2, V1 = (to_host(R[key])[:, :r] for key in ("U1", "U2", "V1"))
+    assert U1.shape == (m1, r) and U2.shape == (m2, r)
+    be = M.backward_error_fro(A1, A2, U1, U2, got, V1)
+    assert be <= 50 * n * U, be
+    for X in (U1, U2, V1):
+        assert M.orthogonality(X) <= 50 * n * U

@@ -303,3 +303,23 @@ def test_complete_2x2_csd_remark_viii(n, cplx):
     X = (A3.conj().T @ (R["U1"] * S[None, :])) + A4.conj().T @ (R["U2"] * C[None, :])
     Qw = np.linalg.qr(X)[0]
     assert np.linalg.norm(A3 + (R["U1"] * S[None, :]) @ Qw.conj().T) > 1e-3
+
+
+# ------------------------------------------------ rectangular blocks (Section 2)
+@pytest.mark.parametrize("m1,m2,n,cplx,k", [(31, 26, 20, False, None), (24, 30, 18, True, None),
+                                           (28, 22, 20, False, 14)])
+def test_rectangular_blocks(m1, m2, n, cplx, k):
+    """A_i of size m_i x n (m_i >= n): the oracle's polar factors are m_i x n,
+    B stays n x n; the known angles, sigma(A1) = cos(theta), the backward
+    error and orthogonality of U_i (m_i x r) hold as in the square case."""
+    A1, A2, th = I.rect_csd(m1, m2, n, seed=m1 + n, cplx=cplx, k=k)
+    R = O.csd(A1, A2)
+    r = n if k is None else k
+    assert R["rank"] == r and R["U1"].shape == (m1, r) and R["U2"].shape == (m2, r)
+    assert np.max(np.abs(R["theta"] - th)) <= 1e-12 * n
+    s1 = np.sort(np.linalg.svd(A1, compute_uv=False))[::-1][:r]
+    assert np.max(np.abs(np.sort(np.cos(R["theta"]))[::-1] - s1)) <= 1e-13
+    be = M.backward_error_fro(A1, A2, R["U1"], R["U2"], R["theta"], R["V1"])
+    assert be <= 50 * n * u
+    for X in (R["U1"], R["U2"], R["V1"]):
+        assert M.orthogonality(X) <= 10 * n * u + 100 * u
