@@ -165,17 +165,19 @@ def _dtype_code(x):
 
 def _colmajor(x):
     """(array, pointer, ld) of a column-major view of the 2-D array x."""
+    # a single column has no meaningful column stride: its ld is m
     if _is_torch(x):
         if x.dim() != 2:
             raise ValueError("expected a 2-D tensor")
         m, n = x.shape
-        if not (x.stride(0) == 1 and x.stride(1) >= max(m, 1)):
+        if not (x.stride(0) == 1 and (n == 1 or x.stride(1) >= max(m, 1))):
             x = x.t().contiguous().t()
-        return x, x.data_ptr(), max(x.stride(1), 1)
+        return x, x.data_ptr(), max(m, 1) if n == 1 else max(x.stride(1), 1)
     x = np.asfortranarray(x)
     if x.ndim != 2:
         raise ValueError("expected a 2-D array")
-    return x, x.ctypes.data, max(x.strides[1] // x.itemsize, 1)
+    m, n = x.shape
+    return x, x.ctypes.data, max(m, 1) if n == 1 else max(x.strides[1] // x.itemsize, 1)
 
 
 def _empty_like2(x, m, n, dtype=None):

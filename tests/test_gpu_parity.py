@@ -401,3 +401,19 @@ def test_csd_rectangular(B, m1, m2, n, cplx, k):
     assert be <= 50 * n * U, be
     for X in (U1, U2, V1):
         assert M.orthogonality(X) <= 50 * n * U
+
+
+@pytest.mark.parametrize("m1,m2,n", [(1, 3, 1), (33, 33, 33), (65, 64, 64), (200, 40, 40)])
+def test_csd_rectangular_edges(B, m1, m2, n):
+    """Edge shapes of csd_polar_rect: n = 1, square blocks through the
+    rectangular entry point, one extra row, a block five times taller."""
+    A1, A2, th = I.rect_csd(m1, m2, n, seed=7 + m1 + m2, cplx=False)
+    R = B.default_context(0).csd_polar_rect(A1, A2)  # host arrays: staged by the library
+    ref = O.csd(A1, A2)
+    assert R["rank"] == n and isinstance(R["U1"], np.ndarray)
+    got = R["theta"][:n]
+    assert np.max(np.abs(got - ref["theta"])) <= 1e-12 * max(n, 1)
+    be = M.backward_error_fro(A1, A2, R["U1"], R["U2"], got, R["V1"])
+    assert be <= 50 * max(n, 2) * U, be
+    for X in (R["U1"], R["U2"], R["V1"]):
+        assert M.orthogonality(X) <= 50 * max(n, 2) * U
