@@ -47,7 +47,44 @@ def parse():
                     help="1 (default): real FP64 products on the tcgen05 tensor cores (exact BF16 slicing); 0: FP64 pipe")
     ap.add_argument("--compare-fp64", type=int, default=1,
                     help="with --tc 1, also time the FP64-pipe path (same workload, same accuracy checks)")
+    ap.add_argument("--config", default="n4096", choices=list(CONFIGS),
+                    help="n4096 (headline), n64 (median of 100 after 10), c2048 (complex rank 1536), n8192")
+    ap.add_argument("--mode", default="csd", choices=["csd", "fp64-peak", "oracle-full"],
+                    help="fp64-peak: DFMA / mma.sync f64 microbenchmark; oracle-full: the CPU oracle once at full size")
     return ap.parse_args()
+
+
+# workload configurations: (n, complex, rank or None, seed)
+CONFIGS = {
+    "n4096": dict(n=4096, cplx=False, rank=None, seed=2, kind="clustered"),
+    "n64": dict(n=64, cplx=False, rank=None, seed=1, kind="haar"),
+    "c2048": dict(n=2048, cplx=True, rank=1536, seed=3, kind="rankdef"),
+    "n8192": dict(n=8192, cplx=False, rank=None, seed=4, kind="clustered"),
+}
+
+
+def workload_name(cfg):
+    n = cfg["n"]
+    if cfg["kind"] == "clustered":
+        return WORKLOAD(n)
+    if cfg["kind"] == "haar":
+        return f"real FP64 CSD n={n}, Haar U1, U2, V, theta i.i.d. U[0, pi/2]"
+    return (f"complex128 partial isometry n={n}, rank {cfg['rank']} ({n - cfg['rank']} zero (C, S) pairs), "
+            f"256 exactly repeated angles, the rest U[0, pi/2] (Algorithm 3)")
+
+
+def make_inputs(cfg, rank_offset=0):
+    from paper_1804_09002_gb300 import inputs as I
+    n, seed = cfg["n"], cfg["seed"] + rank_offset
+    if cfg["kind"] == "clustered":
+        return I.clustered_csd(n, seed=seed)
+    if cfg["kind"] == "haar":
+        return I.haar_csd(n, seed=seed)
+    return I.rankdef_csd(n, cfg["rank"], seed=seed, cplx=True, n_repeat=256)
+
+
+def flops_per_csd(cfg):
+    return FLOPS_PER_CSD(cfg["n"]) * (4.0 if cfg["cplx"] else 1.0)
 
 
 def peaks():
@@ -183,24 +220,30 @@ def cpu_baseline(args):
     O.csd(A1, A2)
     t = time.perf_counter() - t0
     return {"value": t * (args.n / ns) ** 3, "unit": "s/CSD", "cores": OJ.threads(), "kind": "oracle",
-            "sample": f"oracle CSD of one n={ns} instance of the same recipe ({t:.2f} s), scaled by (n/{ns})^3"}
+            "sample": f"oracle CSD of one n={ns} instance of the same recipe ({t:.2f} s), scaled by (n/{ns})^3",
+            "extrapolated": True,
+            "full_size": "bench.py --mode oracle-full times the oracle once at n=4096 (recorded in BASELINE.md)"}
 
 
-def timed_run(args, B, ctx, A1, A2, out, dev, dist, local, profile):
+def timed_run(args, B, ctx, A1, A2, out, dev, dist, local, profile, steps=None, warmup=None):
     """W untimed steps, then K steps between barrier + synchronize, timed with
-    CUDA events on the launching stream; returns (ms, last result, profile,
-    clocks, launches)."""
+    CUDA events on the launching stream (one event pair per step as well);
+    returns (ms total, per-step ms, last result, profile, clocks, launches).
+    With `profile`, every product launch is bracketed by CUDA events (the
+    per-kernel accounting of the roofline); the headline runs without."""
     import torch
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
 
     def step():
         return ctx.csd_polar(A1, A2, out=out)
 
     R = None
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         R = step()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     clocks = ClockSampler(local)
     if profile:
         B.lib.csd_profile_enable(ctx._h, 1)
@@ -209,10 +252,10 @@ def timed_run(args, B, ctx, A1, A2, out, dev, dist, local, profile):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    e0.record(stream)
-    for _ in range(args.steps):
+    ev[0].record(stream)
+    for i in range(steps):
         R = step()
-    e1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -222,25 +265,98 @@ def timed_run(args, B, ctx, A1, A2, out, dev, dist, local, profile):
     if profile:
         B.lib.csd_profile_read(ctx._h, prof)
         B.lib.csd_profile_enable(ctx._h, 0)
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-    return ms, R, prof, ck, launches
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    ms = max_over_ranks(ev[0].elapsed_time(ev[steps]), dist, dev)
+    return ms, per, R, prof, ck, launches
+
+
+def _norm2_sym(E, iters=60):
+    """2-norm of a Hermitian E by power iteration (matrix products only)."""
+    import torch
+    g = torch.Generator(device=E.device).manual_seed(0)
+    v = torch.randn(E.shape[0], 1, dtype=torch.float64, device=E.device, generator=g).to(E.dtype)
+    lam = 0.0
+    for _ in range(iters):
+        w = E @ v
+        lam = float(torch.linalg.norm(w))
+        if lam == 0.0:
+            return 0.0
+        v = w / lam
+    return lam
 
 
 def accuracy(R, A1, A2, th_known, n, dev):
-    """Angles against the generator's, backward error and orthogonality,
-    computed with torch on the GPU (not with the oracle)."""
+    """Angles against the generator's, backward error and orthogonality
+    (Frobenius and 2-norm), computed with torch on the GPU (not with the
+    oracle)."""
     import torch
     rk = R["rank"]
     th = R["theta"][:rk]
-    c, s_ = torch.cos(th), torch.sin(th)
     U1, U2, V1 = (R[k][:, :rk] for k in ("U1", "U2", "V1"))
-    num = torch.sqrt(torch.linalg.norm(A1 - (U1 * c) @ V1.T) ** 2 + torch.linalg.norm(A2 - (U2 * s_) @ V1.T) ** 2)
-    bwd = float(num / np.sqrt(2.0 * n))  # ||A||_F = sqrt(n) for orthonormal columns
+    c, s_ = torch.cos(th).to(U1.dtype), torch.sin(th).to(U1.dtype)
+    Vh = V1.conj().T
+    num = torch.sqrt(torch.linalg.norm(A1 - (U1 * c) @ Vh) ** 2 + torch.linalg.norm(A2 - (U2 * s_) @ Vh) ** 2)
+    den = torch.sqrt(torch.linalg.norm(A1) ** 2 + torch.linalg.norm(A2) ** 2)
+    bwd = float(num / den)
     ang = float(np.max(np.abs(th.cpu().numpy() - th_known)))
-    # Frobenius norm (a plain reduction; the 2-norm would need torch's solver library)
-    orth = max(float(torch.linalg.norm(X.T @ X - torch.eye(rk, device=dev, dtype=X.dtype))) for X in (U1, U2, V1))
+    eye = torch.eye(rk, device=dev, dtype=U1.dtype)
+    orth = max(float(torch.linalg.norm(X.conj().T @ X - eye)) for X in (U1, U2, V1))
+    orth2 = max(_norm2_sym(X.conj().T @ X - eye) for X in (U1, U2, V1))
     return {"max_abs_theta_err_vs_known": ang, "backward_err_fro_over_u": bwd / U, "orth_fro_over_u": orth / U,
-            "rank": rk}
+            "orth_2norm_over_u": orth2 / U, "rank": rk, "bar_over_u": 50 * n}
+
+
+# DRAM traffic of the tensor-core product kernel per launch, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum over every launch of
+# the kernel in one step), with the hash of the kernel source it was taken
+# at; reported only while tc_gemm.cu is unchanged since the capture.
+TRAFFIC = {"tc_gemm": None}
+
+
+def _src_hash(name):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1804_09002_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    t = TRAFFIC.get(kernel)
+    if not t or t.get("src_hash") != _src_hash("tc_gemm.cu"):
+        return None, None
+    return t["bytes_per_launch"], t["profile"]
+
+
+def run_fp64_peak(args):
+    from paper_1804_09002_gb300 import binding as B
+    ck = ClockSampler(0)
+    ck.start()
+    dfma, ms0 = B.fp64_peak(0)
+    dmma, ms1 = B.fp64_peak(1)
+    clocks = ck.stop()
+    print(json.dumps({"mode": "fp64-peak", "dfma_tflops": dfma, "dmma_tflops": dmma, "dfma_best_ms": ms0,
+                      "dmma_best_ms": ms1, "unit_count_peak_tflops": fp64_alu_peak_tflops(), "clocks": clocks}),
+          flush=True)
+
+
+def run_oracle_full(args):
+    """The CPU oracle once at the full size of --config (no extrapolation)."""
+    import platform
+    from oracle import csd as O
+    from oracle import jacobi as OJ
+    cfg = CONFIGS[args.config]
+    A1, A2, _ = make_inputs(cfg)
+    t0 = time.perf_counter()
+    O.csd(A1, A2)
+    t = time.perf_counter() - t0
+    model = ""
+    try:
+        model = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        model = [ln.split(":", 1)[1].strip() for ln in model.splitlines() if ln.startswith("Model name")][0]
+    except Exception:
+        pass
+    print(json.dumps({"mode": "oracle-full", "config": {"workload": workload_name(cfg), "n": cfg["n"]},
+                      "value": t, "unit": "s/CSD", "cores": OJ.threads(), "nproc": os.cpu_count(),
+                      "cpu_model": model, "machine": platform.machine()}), flush=True)
 
 
 def main():
@@ -251,46 +367,65 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
+    if args.mode == "fp64-peak":
+        run_fp64_peak(args)
+        return
+    if args.mode == "oracle-full":
+        run_oracle_full(args)
+        return
     import torch
     from paper_1804_09002_gb300 import binding as B
-    from paper_1804_09002_gb300 import inputs as I
 
+    cfg = CONFIGS[args.config]
+    headline = args.config == "n4096"
+    if args.config == "n64":  # latency case: median of 100 steps after 10 warm-up
+        args.steps = max(args.steps, 100)
+        args.warmup = max(args.warmup, 10)
     # the CPU baseline runs the oracle in worker threads: do it before the
     # first GPU call (rank 0, N = 1 only)
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and headline:
         cpu = cpu_baseline(args)
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    n = args.n
-    A1h, A2h, th_known = I.clustered_csd(n, seed=2 + rank)
+    n = cfg["n"]
+    tdt = torch.complex128 if cfg["cplx"] else torch.float64
+    A1h, A2h, th_known = make_inputs(cfg, rank)
     colmaj = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).to(dev).t()
     A1, A2 = colmaj(A1h), colmaj(A2h)
     ctx = B.Context(local)
     ctx.set_tensor_cores(bool(args.tc))
-    out = {k: torch.empty((n, n), dtype=torch.float64, device=dev).t() for k in ("U1", "U2", "V1")}
+    out = {k: torch.empty((n, n), dtype=tdt, device=dev).t() for k in ("U1", "U2", "V1")}
     out["theta"] = torch.empty(n, dtype=torch.float64, device=dev)
+    fl = flops_per_csd(cfg)
 
-    # ---- headline path (inputs device-resident; A1, A2 = 256 MiB > L2)
-    ms, R, prof, ck, launches = timed_run(args, B, ctx, A1, A2, out, dev, dist, local, True)
+    # ---- headline: profiler off, inputs device-resident
+    ms, per, R, _, ck, launches = timed_run(args, B, ctx, A1, A2, out, dev, dist, local, False)
     s_per_csd = per_csd(ms, args.steps, ws)
+    if args.config == "n64":
+        s_per_csd = statistics.median(per) / 1e3 / ws
     acc = accuracy(R, A1, A2, th_known, n, dev)
+    # ---- one profiled step (CUDA events around every product launch): the
+    # per-kernel and per-site accounting behind the roofline
+    pms, _, _, prof, _, _ = timed_run(args, B, ctx, A1, A2, out, dev, dist, local, True, steps=1, warmup=0)
     # ---- the FP64-pipe path at the same backward-error bar, for comparison
     fp64 = None
-    if args.tc and args.compare_fp64:
+    if args.tc and args.compare_fp64 and not cfg["cplx"]:
         ctx.set_tensor_cores(False)
-        ms64, R64, _, ck64, _ = timed_run(args, B, ctx, A1, A2, out, dev, dist, local, False)
-        fp64 = {"value": per_csd(ms64, args.steps, ws), "unit": "s/CSD",
-                "tflops": FLOPS_PER_CSD(n) * args.steps * ws / (ms64 / 1e3) / 1e12,
+        k64 = 1 if n >= 8192 else args.steps
+        ms64, per64, R64, _, ck64, _ = timed_run(args, B, ctx, A1, A2, out, dev, dist, local, False,
+                                               steps=k64, warmup=1)
+        v64 = per_csd(ms64, k64, ws) if args.config != "n64" else statistics.median(per64) / 1e3 / ws
+        fp64 = {"value": v64, "unit": "s/CSD", "tflops": fl / v64 / 1e12, "steps": k64,
                 "accuracy": accuracy(R64, A1, A2, th_known, n, dev), "clocks": ck64}
-        ctx.set_tensor_cores(True)
+        ctx.set_tensor_cores(bool(args.tc))
     # ---- e2e: same call with pinned host buffers (copies inside the call)
     e2e = None
     if args.e2e_steps > 0:
         A1p = torch.from_numpy(np.ascontiguousarray(A1h.T)).pin_memory().t()
         A2p = torch.from_numpy(np.ascontiguousarray(A2h.T)).pin_memory().t()
-        outp = {k: torch.empty((n, n), dtype=torch.float64).pin_memory().t() for k in ("U1", "U2", "V1")}
+        outp = {k: torch.empty((n, n), dtype=tdt).pin_memory().t() for k in ("U1", "U2", "V1")}
         outp["theta"] = torch.empty(n, dtype=torch.float64).pin_memory()
         ctx.csd_polar(A1p, A2p, out=outp)  # warm the host-buffer path
         if dist:
@@ -301,9 +436,10 @@ def main():
         torch.cuda.synchronize()
         # whole job: the slowest rank's wall time over all ranks' CSDs
         te = max_over_ranks(time.perf_counter() - t0, dist, dev) / (args.e2e_steps * ws)
-        e2e = {"value": te, "unit": "s/CSD", "h2d_bytes_per_step": 2 * n * n * 8,
-               "d2h_bytes_per_step": 3 * n * n * 8 + n * 8}
-    # ---- roofline of the dominant kernel
+        es = 16 if cfg["cplx"] else 8
+        e2e = {"value": te, "unit": "s/CSD", "h2d_bytes_per_step": 2 * n * n * es,
+               "d2h_bytes_per_step": 3 * n * n * es + n * 8}
+    # ---- roofline of the dominant kernel (from the profiled step)
     kinds = ["gemm", "qr_panel", "potrf", "jacobi", "tc_gemm"]
     kms = {k: prof.ms[i] for i, k in enumerate(kinds)}
     dom = max(range(5), key=lambda i: prof.ms[i])
@@ -312,14 +448,17 @@ def main():
     pk = peaks()
     if kinds[dom] == "tc_gemm":
         # 28 BF16 slice products per FP64-equivalent product, against the
-        # measured dense BF16 peak (slicing and FP64 accumulation included in
-        # the kernel time)
+        # measured dense BF16 peak (slicing included in the kernel time)
         peak = pk.get("bf16_tflops_sustained", 1719.1)
-        achieved = 28.0 * flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+        fp64eq = flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+        achieved = 28.0 * fp64eq
+        tr, tr_src = traffic_for("tc_gemm")
         roof = {"kernel": "tc_gemm", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": tr, "traffic_source": tr_src,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
-                "fp64_equivalent_tflops": flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0}
+                "launches_per_step": prof.count[dom], "avg_launch_ms": avg_ms,
+                "fp64_equivalent_tflops": fp64eq, "method_frac_of_bf16_peak": fp64eq / peak,
+                "work_per_launch": "28 x 2mnk BF16 slice flops (2mnk FP64-equivalent) over the tiles executed"}
     else:
         peak = fp64_alu_peak_tflops()
         achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
@@ -327,24 +466,30 @@ def main():
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"}
     products = ("tcgen05 tensor cores, exact BF16 slicing (FP64-accurate), FP64 pipe for the rest" if args.tc
-                else "FP64 FMA pipe")
+                and not cfg["cplx"] else "FP64 FMA pipe")
+    metric = f"s/CSD at n={n} ({'complex128' if cfg['cplx'] else 'FP64'})"
     line = {
-        "metric": "s/CSD at n=4096 (FP64)", "value": s_per_csd, "unit": "s/CSD", "n_gpus": ws,
+        "metric": metric, "value": s_per_csd, "unit": "s/CSD", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "tflops": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12,
-        "tflops_frac_of_fp64_peak": FLOPS_PER_CSD(n) * args.steps * ws / (ms / 1e3) / 1e12 / fp64_alu_peak_tflops(),
-        "config": {"workload": WORKLOAD(n),
-                   "n": n, "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (2 x 128 MiB)",
-                   "products": products},
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if cfg["cplx"] else "f64", "data": "synthetic",
+        "tflops": fl / s_per_csd / 1e12,
+        "tflops_frac_of_fp64_peak": fl / s_per_csd / 1e12 / fp64_alu_peak_tflops(),
+        "config": {"workload": workload_name(cfg), "n": n, "parallelism": f"replicas x{ws}",
+                   "l2": ("inputs larger than L2" if 2 * n * n * (16 if cfg["cplx"] else 8) > 129e6
+                          else "inputs smaller than L2 (latency case)"),
+                   "products": products, "timing": ("median of per-step CUDA-event times" if args.config == "n64"
+                                                    else "CUDA events around K steps, profiler off")},
         "accuracy": acc,
         "roofline": roof,
-        "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
-        "gemm_sites": {nm: {"ms_per_step": prof.site_ms[i] / args.steps,
+        "profiled_step": {"value": pms / 1e3, "unit": "s/CSD",
+                          "note": "one step with CUDA events around every product launch (roofline, sites)"},
+        "kernel_ms_per_step": kms,
+        "gemm_sites": {nm: {"ms_per_step": prof.site_ms[i],
                             "tflops": prof.site_flops[i] / max(prof.site_ms[i], 1e-9) / 1e9,
-                            "launches_per_step": prof.site_count[i] / args.steps}
+                            "launches_per_step": prof.site_count[i]}
                        for i, nm in enumerate(B.csd_profile.SITES) if prof.site_count[i]},
-        "clocks": ck, "gpu_launches": int(launches),
+        "clocks": ck, "gpu_launches": int(launches), "launches_per_csd": launches / args.steps,
     }
     if fp64:
         line["fp64_pipe_path"] = fp64

@@ -38,7 +38,7 @@ extern "C" {
 
 #define CSD_OK 0
 #define CSD_ERR_CUDA 1            /* a CUDA call failed (context may be lost) */
-#define CSD_ERR_NOT_CONVERGED 2   /* Zolo-pd iterate did not converge */
+#define CSD_ERR_NOT_CONVERGED 2   /* polar(): the Zolo-pd iterate did not converge (last iterate written) */
 #define CSD_WARN_ALG2_RCHECK 3    /* Algorithm 2: ||R~ - R|| above tolerance (Section 5.1) */
 #define CSD_ERR_EIG_SPLIT 4       /* Zolo-eig could not split a block after retries */
 #define CSD_ERR_NONFINITE 5       /* input holds NaN or Inf */
@@ -57,12 +57,12 @@ typedef struct {
   int status;             /* same as the return value */
   int rank;               /* detected rank r = round(||A||_F^2) (remark (vi)) */
   double mu;              /* 0 (full rank) or 2 (Algorithm 3) */
-  int zolo_iters;         /* Zolo-pd iterations per polar decomposition */
+  int zolo_iters;         /* Zolo-pd iterations per polar decomposition (polar(): all passes) */
   int r_terms[4];         /* partial-fraction terms r of each iteration */
   double ell[4];          /* lower end l of [l, 1] entering each iteration */
   int chol_fallback;      /* Cholesky iterations redone in QR form */
   int alg2_used[2];       /* Algorithm 2 applied to block i */
-  double orth_err[2];     /* ||W_i^* W_i - I||_F of the Zolo-pd factor */
+  double orth_err[2];     /* ||W_i^* W_i - I||_F of the Zolo-pd factor (polar(): entry 0) */
   double rdiff[2];        /* ||R~_i - R_i||_F / ||R_i||_F (Algorithm 2 check) */
   int eig_splits;         /* Zolo-eig splits performed */
   int eig_retries;        /* splits redone with a perturbed shift */
@@ -229,6 +229,61 @@ int csd_profile_enable(csd_ctx* ctx, int enable);
  * Complex data always uses the FP64 pipe.  Returns 0 or -1 (NULL context). */
 int csd_set_tensor_cores(csd_ctx* ctx, int enable);
 int csd_profile_read(csd_ctx* ctx, csd_profile* out);
+
+/* Zolo-pd iteration control of polar() (Section 5).
+ *   max_extra_passes (0..4, default 1): Section 5's two iterations on
+ *     [eps, 1] converge exactly when every singular value of the (scaled)
+ *     input is at least eps = 1e-15; polar() tests ||W^* W - I||_F <= 50 n u
+ *     afterwards and, when that fails, runs the iteration plan again on the
+ *     current iterate, up to this many times.  If the test still fails the
+ *     call returns CSD_ERR_NOT_CONVERGED with the last iterate in W (and the
+ *     matching H): A is then singular to working precision and has no
+ *     unitary polar factor that the iteration can reach.
+ *   stop_after (default 0): k > 0 makes polar() return the iterate X_k
+ *     after k iterations instead of the polar factor (no convergence test),
+ *     so that callers can check X_k = U Z_k(Sigma) V^*: Zolo-pd's iterates
+ *     share the singular vectors of A (Section 5).
+ * csd_polar, heig and csd_polar_rect are unaffected: in the CS
+ * decomposition an unconverged factor takes Algorithm 2 (Section 5.1).
+ * Returns 0, -1 (NULL context), -2 / -3 (out of range). */
+int csd_set_zolo_control(csd_ctx* ctx, int max_extra_passes, int stop_after);
+
+/* Test hooks (all off by default; none changes results when off).
+ *   flags & CSD_TEST_REJECT_EIG_SPLITS: Zolo-eig rejects every split
+ *     attempt, so a call that needs one retries with every shifted split
+ *     (Section 5's spectral divide and conquer) and then returns
+ *     CSD_ERR_EIG_SPLIT with info->eig_retries filled in.
+ *   tc_probe_wait > 0: every tensor-core kernel launch first polls, this
+ *     many times, an mbarrier that nothing signals, before it issues any
+ *     copy or MMA; the wait runs out, the launch writes NaN outputs, sets
+ *     the device error flag and the call returns CSD_ERR_DEVICE_TIMEOUT.
+ *     The context stays usable.
+ *   tc_flush_every > 0: the tensor-core kernel writes its 64-bit integer
+ *     partial sum out to C every this many 128-k drains (default: every
+ *     120 drains, i.e. only for K > 15 360).
+ * Returns 0, -1 (NULL context), -2 (unknown flag), -3 / -4 (negative). */
+#define CSD_TEST_REJECT_EIG_SPLITS 1u
+int csd_set_test_hooks(csd_ctx* ctx, unsigned flags, long long tc_probe_wait, int tc_flush_every);
+
+/* C = alpha op(A) op(B) + beta C in real FP64 on this library's product
+ * kernels: engine 0 = the FP64-pipe tiles, engine 1 = the tensor-core kernel
+ * (exact BF16 slicing, FP64-accurate; any m, n, k).  The building block of
+ * every step of Zolo-pd and Zolo-eig; it is not itself a step of the paper.
+ *   opA, opB: 0 = N, 1 = T.  A (lda >= rows of A), B (ldb), C (ldc >= m)
+ *   are column-major DEVICE pointers (a host pointer returns -8/-10/-13).
+ * Returns 0, -k for invalid argument k, or CSD_ERR_DEVICE_TIMEOUT /
+ * CSD_ERR_CUDA / CSD_ERR_ALLOC. */
+int csd_gemm(csd_ctx* ctx, int opA, int opB, int m, int n, int k, double alpha, const double* A, int lda,
+             const double* B, int ldb, double beta, double* C, int ldc, int engine);
+
+/* FP64 peak microbenchmark (the FP64 roofline's denominator; not a step of
+ * the paper): kind 0 = DFMA loop on the FMA pipe, kind 1 = mma.sync
+ * m8n8k4 f64 loop, 8 CTAs of 256 threads per SM, 8 independent chains per
+ * thread; best of 10 timed launches (CUDA events) after one warm-up.
+ * *tflops receives the rate, *ms (may be NULL) the best launch time.
+ * Allocates and frees a small device buffer.  Returns 0, -k for invalid
+ * argument k, or CSD_ERR_CUDA / CSD_ERR_ALLOC. */
+int csd_fp64_peak(int device, int kind, double* tflops, double* ms);
 
 /* Process-wide number of kernels this library has launched so far. */
 long long csd_launch_count(void);

@@ -86,13 +86,18 @@ def _load():
     lib.csd_complete_v2.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, vp, ci, vp, vp, ci,
                                     ctypes.POINTER(csd_info)]
     lib.csd_profile_read.argtypes = [vp, ctypes.POINTER(csd_profile)]
+    lib.csd_set_zolo_control.argtypes = [vp, ci, ci]
+    lib.csd_set_test_hooks.argtypes = [vp, ctypes.c_uint, ctypes.c_longlong, ci]
+    lib.csd_gemm.argtypes = [vp, ci, ci, ci, ci, ci, cd, vp, ci, vp, ci, cd, vp, ci, ci]
+    lib.csd_fp64_peak.argtypes = [ci, ci, ctypes.POINTER(cd), ctypes.POINTER(cd)]
     lib.csd_launch_count.argtypes = []
     lib.csd_launch_count.restype = ctypes.c_longlong
     lib.csd_status_str.argtypes = [ci]
     lib.csd_status_str.restype = ctypes.c_char_p
     for f in ("csd_create", "csd_set_stream", "csd_destroy", "csd_polar", "polar", "heig", "zolo_coeffs",
               "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc", "csd_set_tensor_cores",
-              "csd_set_theta_mode", "csd_complete_v2", "csd_polar_rect"):
+              "csd_set_theta_mode", "csd_complete_v2", "csd_polar_rect", "csd_set_zolo_control",
+              "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak"):
         getattr(lib, f).restype = ci
     return lib
 
@@ -102,13 +107,17 @@ lib = _load()
 EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes", "csd_polar", "polar", "heig",
             "zolo_coeffs", "zolo_plan", "csd_status_str", "csd_profile_enable", "csd_profile_read",
             "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores", "csd_set_theta_mode", "csd_complete_v2",
-            "csd_polar_rect"]
+            "csd_polar_rect", "csd_set_zolo_control", "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak"]
+
+STATUS_NOT_CONVERGED = 2
+TEST_REJECT_EIG_SPLITS = 1
 
 
 class CSDError(RuntimeError):
-    def __init__(self, status, where):
+    def __init__(self, status, where, info=None):
         super().__init__(f"{where}: status {status} ({lib.csd_status_str(status).decode()})")
         self.status = status
+        self.info = info
 
 
 # ------------------------------------------------------------------ host-only
@@ -132,6 +141,17 @@ def zolo_plan(ell0=1e-15, rmax=8, max_iter=4):
     if k < 0:
         raise CSDError(k, "zolo_plan")
     return r[:k].tolist(), ell[:k].tolist()
+
+
+def fp64_peak(kind=0, device=0):
+    """Measured FP64 rate (TFLOP/s, best launch ms): kind 0 = DFMA loop,
+    1 = mma.sync f64 loop."""
+    t = ctypes.c_double()
+    ms = ctypes.c_double()
+    st = lib.csd_fp64_peak(int(device), int(kind), ctypes.byref(t), ctypes.byref(ms))
+    if st != 0:
+        raise CSDError(st, "csd_fp64_peak")
+    return t.value, ms.value
 
 
 # ------------------------------------------------------------------ arrays
@@ -245,6 +265,41 @@ class Context:
         if st != 0:
             raise CSDError(st, "csd_set_theta_mode")
 
+    def set_zolo_control(self, max_extra_passes=1, stop_after=0):
+        """polar(): further plan passes when the iterate has not converged
+        (default 1); stop_after = k > 0 returns the k-th Zolo-pd iterate."""
+        st = lib.csd_set_zolo_control(self._h, int(max_extra_passes), int(stop_after))
+        if st != 0:
+            raise CSDError(st, "csd_set_zolo_control")
+
+    def set_test_hooks(self, flags=0, tc_probe_wait=0, tc_flush_every=0):
+        """Failure-path test hooks (host-side split rejection, a tensor-core
+        wait that runs out, int64 write-outs every few drains); 0 = off."""
+        st = lib.csd_set_test_hooks(self._h, int(flags), int(tc_probe_wait), int(tc_flush_every))
+        if st != 0:
+            raise CSDError(st, "csd_set_test_hooks")
+
+    def gemm(self, A, B, C=None, alpha=1.0, beta=0.0, opA=0, opB=0, engine=1):
+        """C = alpha op(A) op(B) + beta C on the library's FP64 product
+        kernels (engine 0: FP64 pipe, 1: tensor cores); float64 CUDA tensors."""
+        if not (_is_torch(A) and A.is_cuda):
+            raise TypeError("csd_gemm takes CUDA tensors")
+        A, pa, la = _colmajor(A)
+        B, pb, lb = _colmajor(B)
+        m = A.shape[0] if opA == 0 else A.shape[1]
+        k = A.shape[1] if opA == 0 else A.shape[0]
+        n = B.shape[1] if opB == 0 else B.shape[0]
+        if C is None:
+            C = _empty_like2(A, m, n)
+            C.zero_()
+        C, pc, lc = _colmajor(C)
+        self._bind_stream(A)
+        st = lib.csd_gemm(self._h, int(opA), int(opB), m, n, k, float(alpha), pa, la, pb, lb, float(beta), pc, lc,
+                          int(engine))
+        if st != 0:
+            raise CSDError(st, "csd_gemm")
+        return C
+
     def complete_v2(self, A3, A4, U1, U2, theta):
         """V2 of the complete 2 x 2 CSD of a unitary [A1 A3; A2 A4] from the
         U1, U2, theta of [A1; A2] (remark (viii))."""
@@ -291,7 +346,7 @@ class Context:
         st = lib.csd_polar(self._h, dt, n, p1, l1, p2, l2, pu1, lu1, pu2, lu2, pv1, lv1, _ptr(theta),
                            ctypes.byref(rank), ctypes.byref(info))
         if st not in (STATUS_OK, WARN_ALG2_RCHECK):
-            raise CSDError(st, "csd_polar")
+            raise CSDError(st, "csd_polar", info.as_dict())
         return dict(U1=U1, U2=U2, V1=V1, theta=theta, rank=rank.value, info=info.as_dict(), status=st)
 
     def csd_polar_rect(self, A1, A2):
@@ -319,7 +374,10 @@ class Context:
             raise CSDError(st, "csd_polar_rect")
         return dict(U1=U1, U2=U2, V1=V1, theta=theta, rank=rank.value, info=info.as_dict(), status=st)
 
-    def polar(self, A, want_h=True):
+    def polar(self, A, want_h=True, allow_not_converged=False):
+        """(W, H, info).  CSD_ERR_NOT_CONVERGED raises unless
+        allow_not_converged, in which case the last iterate is returned and
+        info["status"] says so."""
         dt = _dtype_code(A)
         A, pa, la = _colmajor(A)
         n = A.shape[1]
@@ -328,8 +386,8 @@ class Context:
         info = csd_info()
         self._bind_stream(A)
         st = lib.polar(self._h, dt, n, pa, la, _ptr(W), n, _ptr(H) if want_h else None, n, ctypes.byref(info))
-        if st != STATUS_OK:
-            raise CSDError(st, "polar")
+        if st != STATUS_OK and not (allow_not_converged and st == STATUS_NOT_CONVERGED):
+            raise CSDError(st, "polar", info.as_dict())
         return W, H, info.as_dict()
 
     def heig(self, B):
@@ -342,7 +400,7 @@ class Context:
         self._bind_stream(B)
         st = lib.heig(self._h, dt, n, pb, lb, _ptr(lam), _ptr(V), n, ctypes.byref(info))
         if st != STATUS_OK:
-            raise CSDError(st, "heig")
+            raise CSDError(st, "heig", info.as_dict())
         return lam, V, info.as_dict()
 
 

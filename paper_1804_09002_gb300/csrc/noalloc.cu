@@ -11,6 +11,7 @@
 
 #include "../../include/zolo_csd.h"
 #include "solver.h"
+#include "tc_gemm.h"
 
 namespace zcsd {
 
@@ -56,8 +57,25 @@ bool on_device(const void* p) {
 thread_local double t_hd[64];
 thread_local int t_hi[4096];
 
+// The call runs polar_impl (the polar() entry point's body) on an arena over
+// the static scratch.  The thread's tensor-core dispatch state and profiler
+// are switched off for the call and restored afterwards, so a product can
+// never draw slices from another call's arena (n <= 64 is also below the
+// tensor-core kernel's smallest tile).
 template <class T>
 int polar_noalloc_impl(int n, const T* A, int lda, T* Wo, int ldw, T* Ho, int ldh, cudaStream_t st, void* base) {
+  struct StateScope {
+    TcState tc;
+    Profiler* prof;
+    StateScope() : tc(t_tc), prof(t_prof) {
+      t_tc = TcState{};
+      t_prof = nullptr;
+    }
+    ~StateScope() {
+      t_tc = tc;
+      t_prof = prof;
+    }
+  } scope;
   Ctx cx;
   cx.stream = st;
   cx.hs.d = t_hd;
@@ -65,27 +83,7 @@ int polar_noalloc_impl(int n, const T* A, int lda, T* Wo, int ldw, T* Ho, int ld
   Arena ar;
   ar.base = static_cast<char*>(base);
   ar.cap = NOALLOC_BYTES;
-  const long long nn = (long long)n * n;
-  T* X = ar.get<T>(nn);
-  T* W = ar.get<T>(nn);
-  double* sc = ar.get<double>(64);
-  double* scratch = ar.get<double>(304 * 4);
-  axpby<T>(st, n, n, 1.0, A, lda, 0, 0.0, X, n, 0, 1);
-  count_nonfinite<T>(st, n, n, X, n, sc, scratch);
-  fro2<T>(st, n, n, X, n, 0, 0.0, sc + 1, 1, scratch);
-  d2h(cx, cx.hs.d, sc, 2 * sizeof(double));
-  if (cx.hs.d[0] != 0.0) return CSD_ERR_NONFINITE;
-  const double fn = std::sqrt(cx.hs.d[1]);
-  const double alpha = (fn > 1.0) ? 1.0 / fn : 1.0;
-  if (alpha != 1.0) axpby<T>(st, n, n, alpha, X, n, 0, 0.0, X, n, 0, 1);
-  zolo_pd<T>(cx, ar, n, 1, X, W, nullptr);
-  axpby<T>(st, n, n, 1.0, W, n, 0, 0.0, Wo, ldw, 0, 1);
-  if (Ho) {
-    gemm1<T>(st, OP_C, OP_N, n, n, n, from_re<T>(1.0), W, n, A, lda, zero<T>(), X, n);
-    symmetrize<T>(st, n, X, n, 0, Ho, ldh, 0, 1);
-  }
-  ZCSD_CUDA(cudaStreamSynchronize(st));
-  return CSD_OK;
+  return polar_impl<T>(cx, ar, n, A, lda, Wo, ldw, Ho, ldh, nullptr);
 }
 
 }  // namespace

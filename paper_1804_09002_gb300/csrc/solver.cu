@@ -104,9 +104,10 @@ void d2h(Ctx& cx, void* dst, const void* src, size_t bytes) {
 // iteration in QR form (X (X^*X + cI)^{-1} = Q1 Q2^* / sqrt(c) for
 // [X; sqrt(c) I] = [Q1; Q2] R), later ones in Cholesky form.
 template <class T>
-void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd) {
+void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after) {
   cudaStream_t st = cx.stream;
   const Plan& pl = get_plan(cx);
+  const int steps = (stop_after > 0) ? std::min(stop_after, pl.steps) : pl.steps;
   const long long nn = (long long)n * n;
   const size_t mk = ar.mark();
   T* Xa = ar.get<T>(nn * P);
@@ -115,9 +116,10 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd)
   T* X = Xa;
   T* Xn = Xb;
   const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zer = zero<T>();
-  for (int s = 0; s < pl.steps; ++s) {
+  for (int s = 0; s < steps; ++s) {
     const int r = pl.r[s];
     bool use_qr = (s == 0);
+    if (pd) pd->iters += 1;
     for (int attempt = 0; attempt < 2; ++attempt) {
       const size_t mk2 = ar.mark();
       if (use_qr) {
@@ -192,8 +194,8 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd)
   ar.release(mk);
 }
 
-template void zolo_pd<double>(Ctx&, Arena&, int, int, const double*, double*, PolarDiag*);
-template void zolo_pd<z64>(Ctx&, Arena&, int, int, const z64*, z64*, PolarDiag*);
+template void zolo_pd<double>(Ctx&, Arena&, int, int, const double*, double*, PolarDiag*, int);
+template void zolo_pd<z64>(Ctx&, Arena&, int, int, const z64*, z64*, PolarDiag*, int);
 
 // ---------------------------------------------------------------- Zolo-eig
 struct EigDiag {
@@ -335,6 +337,7 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
       const double offa = std::sqrt(cx.hs.d[0]);
       if (debug) fprintf(stderr, "zolo-eig:   k=%d ||B21||=%.3e tol=%.3e\n", k, offa, off_tol);
       if (!(offa <= off_tol)) continue;
+      if (cx.test_flags & TEST_REJECT_EIG_SPLITS) continue;  // injected failure (tests only)
       ed->offblock = std::max(ed->offblock, offa / std::max(bnorm, 1e-300));
       ed->splits += 1;
       // accept: B_sub <- B' (+ s I), V[:, off:off+sz] <- V[:, off:off+sz] Q
@@ -352,7 +355,7 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
     }
     if (!done) {
       ed->status = CSD_ERR_EIG_SPLIT;
-      throw ed;
+      throw EigFail{ed->splits, ed->retries};
     }
   }
   // ---- leaves: Jacobi on blocks <= LEAF; scalar blocks keep their diagonal
@@ -715,6 +718,29 @@ int csd_rect_impl(Ctx& cx, Arena& ar, int m1, int m2, int n, const T* A1, int ld
   return stt;
 }
 
+// ||W^* W - I||_F of the n x n W (device) read back to the host.
+template <class T>
+static double orth_error(Ctx& cx, Arena& ar, int n, const T* W, double* sc, double* scratch) {
+  const size_t mk = ar.mark();
+  T* G = ar.get<T>((size_t)n * n);
+  gemm1<T>(cx.stream, OP_C, OP_N, n, n, n, from_re<T>(1.0), W, n, W, n, zero<T>(), G, n, 0, 0, GS_ORTH);
+  fro2<T>(cx.stream, n, n, G, n, 0, 1.0, sc, 1, scratch);
+  d2h(cx, cx.hs.d, sc, sizeof(double));
+  ar.release(mk);
+  return std::sqrt(cx.hs.d[0]);
+}
+
+// polar(): Zolo-pd on [eps, 1] (Section 5.1), then the convergence test.
+// Section 5 runs two iterations; with the interval fixed in advance they
+// converge exactly when every singular value of the scaled A is at least
+// eps, and otherwise the iterate is not unitary.  The test is therefore
+// ||X^* X - I||_F <= 50 n u after the planned iterations.  A failing iterate
+// goes through the plan again (its smallest singular values have grown by
+// the slope of the composed map near zero, so one more pass converges
+// unless A is singular to working precision), up to cx.zolo_extra_passes
+// times; if it still fails, the call returns CSD_ERR_NOT_CONVERGED with the
+// last iterate written.  cx.zolo_stop_after > 0 returns the iterate X_k
+// itself (no test), for checking the iterates against U Z_k(Sigma) V^*.
 template <class T>
 int polar_impl(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* Wo, int ldw, T* Ho, int ldh, csd_info* info) {
   cudaStream_t st = cx.stream;
@@ -733,7 +759,20 @@ int polar_impl(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* Wo, int ldw, T
   const double alpha = (fn > 1.0) ? 1.0 / fn : 1.0;
   if (alpha != 1.0) axpby<T>(st, n, n, alpha, X, n, 0, 0.0, X, n, 0, 1);
   PolarDiag pd;
-  zolo_pd<T>(cx, ar, n, 1, X, W, &pd);
+  int status = CSD_OK;
+  double orth = 0.0;
+  if (cx.zolo_stop_after > 0) {
+    zolo_pd<T>(cx, ar, n, 1, X, W, &pd, cx.zolo_stop_after);
+  } else {
+    zolo_pd<T>(cx, ar, n, 1, X, W, &pd);
+    const double tol = 50.0 * n * U_ROUND;
+    orth = orth_error<T>(cx, ar, n, W, sc + 2, scratch);
+    for (int pass = 0; pass < cx.zolo_extra_passes && !(orth <= tol); ++pass) {
+      zolo_pd<T>(cx, ar, n, 1, W, W, &pd);
+      orth = orth_error<T>(cx, ar, n, W, sc + 2, scratch);
+    }
+    if (!(orth <= tol)) status = CSD_ERR_NOT_CONVERGED;
+  }
   axpby<T>(st, n, n, 1.0, W, n, 0, 0.0, Wo, ldw, 0, 1);
   if (Ho) {
     T* Hm = X;
@@ -742,16 +781,20 @@ int polar_impl(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* Wo, int ldw, T
   }
   if (info) {
     const Plan& pl = get_plan(cx);
-    info->zolo_iters = pl.steps;
+    info->zolo_iters = pd.iters;
     for (int s = 0; s < 4; ++s) {
       info->r_terms[s] = s < pl.steps ? pl.r[s] : 0;
       info->ell[s] = s < pl.steps ? pl.ell[s] : 0.0;
     }
     info->chol_fallback = pd.chol_fallback;
+    info->orth_err[0] = orth;
   }
   ZCSD_CUDA(cudaStreamSynchronize(st));
-  return CSD_OK;
+  return status;
 }
+
+template int polar_impl<double>(Ctx&, Arena&, int, const double*, int, double*, int, double*, int, csd_info*);
+template int polar_impl<z64>(Ctx&, Arena&, int, const z64*, int, z64*, int, z64*, int, csd_info*);
 
 template <class T>
 int heig_entry(Ctx& cx, Arena& ar, int n, const T* B, int ldb, double* lam, T* Vo, int ldv, csd_info* info) {
@@ -869,7 +912,7 @@ int run_with_ws(Ctx& cx, size_t need, csd_info* info, F body) {
     ar.cap = cx.ws_bytes;
     try {
       int* tc_err = nullptr;
-      if (cx.tensor_cores) {
+      if (cx.tensor_cores || cx.force_tc_err) {
         tc_err = ar.get<int>(1);
         ZCSD_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int), cx.stream));
       }
@@ -877,12 +920,16 @@ int run_with_ws(Ctx& cx, size_t need, csd_info* info, F body) {
       t_tc.sites = cx.tc_sites;
       t_tc.ar = &ar;
       t_tc.err = tc_err;
+      t_tc.probe_wait = cx.tc_probe_wait;
+      t_tc.flush_every = cx.tc_flush_every;
       status = body(ar);
       if (tc_err) {
         int h = 0;
         ZCSD_CUDA(cudaMemcpyAsync(&h, tc_err, sizeof(int), cudaMemcpyDeviceToHost, cx.stream));
         ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
-        if (h && (status == CSD_OK || status == CSD_WARN_ALG2_RCHECK)) status = CSD_ERR_DEVICE_TIMEOUT;
+        // a timed-out product leaves NaN behind, which later steps may report
+        // in their own way; the timeout is the cause
+        if (h && status != CSD_ERR_CUDA) status = CSD_ERR_DEVICE_TIMEOUT;
       }
       break;
     } catch (ArenaOverflow& o) {
@@ -893,8 +940,12 @@ int run_with_ws(Ctx& cx, size_t need, csd_info* info, F body) {
       fprintf(stderr, "zolo_csd: CUDA error %s at %s:%d\n", cudaGetErrorString(f.err), f.file, f.line);
       status = CSD_ERR_CUDA;
       break;
-    } catch (EigDiag*) {
+    } catch (EigFail& e) {
       status = CSD_ERR_EIG_SPLIT;
+      if (info) {
+        info->eig_splits = e.splits;
+        info->eig_retries = e.retries;
+      }
       break;
     } catch (std::bad_alloc&) {
       status = CSD_ERR_ALLOC;
@@ -993,7 +1044,7 @@ int polar_typed(csd_ctx* ctx, int n, const void* A, int lda, void* W, int ldw, v
     Mat<T> h;
     if (H) h = view_out<T>(ar, H, ldh, n, n);
     int st = polar_impl<T>(cx, ar, n, a.d, a.ld, w.d, w.ld, H ? h.d : nullptr, h.ld, info);
-    if (st == CSD_OK) {
+    if (st == CSD_OK || st == CSD_ERR_NOT_CONVERGED) {
       copy_out(cx, w, n, n);
       if (H) copy_out(cx, h, n, n);
       ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
@@ -1067,9 +1118,79 @@ int complete_v2_typed(csd_ctx* ctx, int n, const void* A3, int lda3, const void*
   });
 }
 
+// C = alpha op(A) op(B) + beta C on the FP64 pipe (engine 0) or the
+// tensor-core kernel (engine 1, any shape).
+int gemm_typed(csd_ctx* ctx, int opA, int opB, int m, int n, int k, double alpha, const double* A, int lda,
+               const double* B, int ldb, double beta, double* C, int ldc, int engine) {
+  Ctx& cx = ctx->cx;
+  const size_t need = (size_t)16 * ((size_t)(m + 128) * (k + 64) + (size_t)(n + 128) * (k + 64)) + (1 << 20);
+  cx.force_tc_err = engine == 1;
+  const int st = run_with_ws(cx, need, nullptr, [&](Arena& ar) -> int {
+    GemmArgs<double> g;
+    g.m = m; g.n = n; g.k = k; g.opA = opA; g.opB = opB;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
+    g.Cin = C; g.ldcin = ldc; g.C = C; g.ldc = ldc;
+    g.alpha = alpha; g.beta = beta;
+    if (engine == 1) {
+      tc_gemm(g, cx.stream, ar, t_tc.err);
+    } else {
+      t_tc.enabled = false;
+      gemm(g, cx.stream);
+    }
+    ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+    return CSD_OK;
+  });
+  cx.force_tc_err = false;
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
+
+int csd_set_zolo_control(csd_ctx* ctx, int max_extra_passes, int stop_after) {
+  if (!ctx) return -1;
+  if (max_extra_passes < 0 || max_extra_passes > 4) return -2;
+  if (stop_after < 0) return -3;
+  ctx->cx.zolo_extra_passes = max_extra_passes;
+  ctx->cx.zolo_stop_after = stop_after;
+  return CSD_OK;
+}
+
+int csd_set_test_hooks(csd_ctx* ctx, unsigned flags, long long tc_probe_wait, int tc_flush_every) {
+  if (!ctx) return -1;
+  if (flags & ~(unsigned)CSD_TEST_REJECT_EIG_SPLITS) return -2;
+  if (tc_probe_wait < 0) return -3;
+  if (tc_flush_every < 0) return -4;
+  ctx->cx.test_flags = flags;
+  ctx->cx.tc_probe_wait = tc_probe_wait;
+  ctx->cx.tc_flush_every = tc_flush_every;
+  return CSD_OK;
+}
+
+int csd_gemm(csd_ctx* ctx, int opA, int opB, int m, int n, int k, double alpha, const double* A, int lda,
+             const double* B, int ldb, double beta, double* C, int ldc, int engine) {
+  if (!ctx) return -1;
+  if (opA != 0 && opA != 1) return -2;
+  if (opB != 0 && opB != 1) return -3;
+  if (m < 0) return -4;
+  if (n < 0) return -5;
+  if (k < 0) return -6;
+  const int ra = opA == 0 ? m : k, rb = opB == 0 ? k : n;
+  if (k > 0 && m > 0 && !is_device_ptr(A)) return -8;
+  if (lda < std::max(1, ra)) return -9;
+  if (k > 0 && n > 0 && !is_device_ptr(B)) return -10;
+  if (ldb < std::max(1, rb)) return -11;
+  if (m > 0 && n > 0 && !is_device_ptr(C)) return -13;
+  if (ldc < std::max(1, m)) return -14;
+  if (engine != 0 && engine != 1) return -15;
+  if (m == 0 || n == 0) return CSD_OK;
+  if (k == 0) {
+    if (beta == 1.0) return CSD_OK;
+    return gemm_typed(ctx, opA, opB, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc, 0);
+  }
+  return gemm_typed(ctx, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, engine);
+}
 
 int csd_create(csd_ctx** ctx, int device, void* stream) {
   if (!ctx) return -1;

@@ -2,6 +2,7 @@
 #pragma once
 #include "linalg.h"
 #include "profile.h"
+#include "../../include/zolo_csd.h"
 
 namespace zcsd {
 
@@ -31,10 +32,28 @@ struct Ctx {
   bool tensor_cores = false;
   unsigned tc_sites = 0;
   int theta_mode = 0;  // 0: atan2(S, C) (remark (iii)); 1: from Lambda (remark (iv))
+  int zolo_extra_passes = 1;  // polar(): further passes of the plan when the iterate has not converged
+  int zolo_stop_after = 0;    // polar(): > 0 returns the iterate X_k after k iterations (k <= plan steps)
+  unsigned test_flags = 0;    // TEST_* below (fault injection on the host; default off)
+  long long tc_probe_wait = 0;  // tensor-core kernel: polls of a barrier nothing signals (0 = none)
+  int tc_flush_every = 0;       // tensor-core kernel: drains between int64 write-outs (0 = default)
+  bool force_tc_err = false;    // the running call needs the tensor-core error flag (csd_gemm)
+};
+
+// Host-side fault injection for the failure-path tests.
+enum TestFlags : unsigned {
+  TEST_REJECT_EIG_SPLITS = CSD_TEST_REJECT_EIG_SPLITS,  // Zolo-eig treats every split attempt as rejected
 };
 
 struct PolarDiag {
   int chol_fallback = 0;
+  int iters = 0;  // Zolo-pd iterations run
+};
+
+// A Zolo-eig block that could not be split after every retry; thrown by
+// value so the entry point can report the counts.
+struct EigFail {
+  int splits, retries;
 };
 
 const Plan& get_plan(Ctx& cx);
@@ -43,7 +62,13 @@ void d2h(Ctx& cx, void* dst, const void* src, size_t bytes);
 
 // W_p = polar factor of X0_p for p < P (Zolo-pd, Section 5); X0 and W are
 // P consecutive n x n matrices (ld n).  Workspace comes from `ar`.
+// stop_after > 0 stops after that many iterations (the iterate X_k).
 template <class T>
-void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd);
+void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after = 0);
+
+// The polar() entry point on an arena the caller provides (also used by the
+// allocation-free entry point).  Returns a CSD_* status.
+template <class T>
+int polar_impl(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* Wo, int ldw, T* Ho, int ldh, csd_info* info);
 
 }  // namespace zcsd

@@ -83,9 +83,9 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t phase, long long limit = TC_WAIT_LIMIT) {
   uint32_t done = 0;
-  for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
+  for (long long it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -199,6 +199,8 @@ struct TcArgs {
   const double* Cin; int ldcin; long long sCin; int bdivC;
   double* C; int ldc; long long sC;
   int* err;
+  int max_drains;          // drains between write-outs of the int64 sum
+  long long probe_wait;    // > 0: first poll a barrier nothing signals (timeout-path tests)
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
   unsigned char* sB = smem + 2 * TC_STAGE_A;
-  __shared__ __align__(8) uint64_t mbar[2];  // MMA completion of the stage in buffer 0 / 1
+  __shared__ __align__(8) uint64_t mbar[3];  // MMA completion of the stage in buffer 0 / 1; [2]: probe
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int z = blockIdx.z;
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[2])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -252,6 +255,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
     for (int c = 0; c < TC_CPT; c += 16) ifix_store16(tmem_row, c, z16);
   }
   bool ok = true;
+  if (g.probe_wait > 0) {
+    // test hook: a bounded wait on a barrier that nothing signals, before
+    // any copy or MMA is issued; it runs out and the launch takes the
+    // timeout path (NaN outputs, error flag)
+    ok = __syncthreads_and(tid != 0 || mbar_wait(smem_u32(&mbar[2]), 0u, g.probe_wait)) != 0;
+  }
   // accumulator a at TMEM columns [64 a, 64 a + 64): a = g - 2 for g <= 6, a = 5 for g >= 7
   uint32_t filled = 0;  // bit a set: accumulator a holds data since its last drain
   int chunks_since_drain = 0, nchunks = 0, ndrain = 0;
@@ -342,7 +351,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
       if (ok) {
         // |I| grows by < 2^56.1 per drain: every TC_MAX_DRAINS drains the
         // partial sum is written out before it can leave int64 (K > ~15k)
-        const bool flush = ++ndrain == TC_MAX_DRAINS;
+        const bool flush = ++ndrain == g.max_drains;
 #pragma unroll
         for (int c = 0; c < TC_CPT; c += 16) {
           long long I[16];
@@ -625,6 +634,8 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   t.kb_flags = g.kflags; t.ksplit = std::max(1, g.ksplit); t.uplo = g.uplo; t.alpha = re(g.alpha); t.beta = re(g.beta);
   t.Cin = g.Cin; t.ldcin = g.ldcin; t.sCin = g.sCin; t.bdivC = g.bdivC;
   t.C = g.C; t.ldc = g.ldc; t.sC = g.sC; t.err = err;
+  t.max_drains = t_tc.flush_every > 0 ? std::min(t_tc.flush_every, TC_MAX_DRAINS) : TC_MAX_DRAINS;
+  t.probe_wait = t_tc.probe_wait;
   ZCSD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   dim3 grid(mpad / TC_BM, npad / TC_BN, g.batch * t.ksplit);
   tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(t);

@@ -15,6 +15,8 @@ struct TcState {
   unsigned sites = 0;  // bit s: GEMM call site s (GemmSite) may run on the tensor cores
   Arena* ar = nullptr;
   int* err = nullptr;
+  long long probe_wait = 0;  // > 0: each launch first polls a barrier nothing signals (timeout-path tests)
+  int flush_every = 0;       // > 0: drains between write-outs of the int64 sum (flush-path tests)
 };
 extern thread_local TcState t_tc;
 // true when gemm<double>(g) will run on the tensor cores

@@ -49,6 +49,9 @@ def test_bad_arguments_are_rejected_without_a_device(B):
     assert lib.csd_polar_rect(None, 0, 8, 8, 4, None, 8, None, 8, None, 8, None, 8, None, 4, None, None, None) == -1
     assert lib.zolo_coeffs(0.0, 8, None, None, None, None) == -1
     assert lib.zolo_coeffs(0.5, 0, None, None, None, None) == -2
+    assert lib.csd_set_zolo_control(None, 1, 0) == -1
+    assert lib.csd_set_test_hooks(None, 0, 0, 0) == -1
+    assert lib.csd_gemm(None, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 1) == -1
     assert B.lib.csd_status_str(-3) == b"invalid argument"
 
 

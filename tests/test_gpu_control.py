@@ -1,0 +1,232 @@
+"""Convergence test of Zolo-pd, its individual iterates, the product kernels
+against the plain definition of a matrix product, and the failure paths
+(host-side fault injection and a bounded device wait that runs out).
+
+* Section 5: Zolo-pd's iterates share A's singular vectors,
+  X_k = U Z_k(Sigma) V^*, with Z_k the composition of the scalar Zolotarev
+  maps; oracle/zolo.py evaluates those maps in 50-digit arithmetic.
+* Section 5.1: on [eps, 1] two iterations converge exactly when
+  sigma_min >= eps; below that, polar() runs the plan again or reports
+  CSD_ERR_NOT_CONVERGED.
+"""
+import numpy as np
+import pytest
+
+from oracle import zolo as Z
+from tests.gpu_util import U, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_09002_gb300 import binding
+    return binding
+
+
+def _haar(n, rng):
+    Q, R = np.linalg.qr(rng.standard_normal((n, n)))
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def _with_sv(n, sigma, seed):
+    rng = np.random.default_rng(seed)
+    Uo, Vo = _haar(n, rng), _haar(n, rng)
+    return (Uo * sigma[None, :]) @ Vo.T, (Uo, sigma, Vo)
+
+
+# ------------------------------------------------------------------ iterates
+@pytest.mark.parametrize("n,tc", [(64, False), (257, False), (257, True)])
+def test_zolo_pd_iterates_match_scalar_maps(B, n, tc):
+    """X_1 and X_2 of the GPU iteration against U Z_k(Sigma) V^* (Section 5),
+    sigma spread over [1e-2, 1]: a wrong coefficient, weight or term changes
+    X_1 by far more than the 1e-10 tolerance (the iterate's own conditioning
+    on this interval allows about 1e2 n u)."""
+    A, svd = _with_sv(n, np.geomspace(1e-2, 1.0, n), seed=n)
+    steps = Z.plan(1e-15)
+    want = Z.expected_iterates(A, steps, svd)
+    ctx = B.Context(0)
+    try:
+        ctx.set_tensor_cores(tc)
+        for k in (1, 2):
+            ctx.set_zolo_control(1, k)
+            X, _, info = ctx.polar(to_dev(A), want_h=False)
+            assert info["zolo_iters"] == k
+            err = np.linalg.norm(to_host(X) - want[k - 1])
+            assert err <= 1e-10, (k, err)
+        # X_1 is not unitary (its singular values lie in [Z_1(1e-2), 1]),
+        # X_2 is the polar factor
+        assert np.linalg.norm(want[0].T @ want[0] - np.eye(n)) > 1e-3
+        assert np.linalg.norm(want[1] - svd[0] @ svd[2].T) <= 1e-12 * n
+    finally:
+        ctx.close()
+
+
+# ------------------------------------------------------------------ convergence
+def test_polar_below_eps_takes_another_pass(B):
+    """sigma_min = 1e-18 < eps: the planned two iterations leave W not
+    unitary; polar() runs the plan again and converges (4 iterations).
+    With no extra pass allowed it reports CSD_ERR_NOT_CONVERGED and still
+    writes the iterate."""
+    n = 64
+    A, (Uo, s, Vo) = _with_sv(n, np.geomspace(1e-18, 1.0, n), seed=11)
+    ctx = B.Context(0)
+    try:
+        W, H, info = ctx.polar(to_dev(A))
+        W, H = to_host(W), to_host(H)
+        assert info["zolo_iters"] == 4
+        assert np.linalg.norm(W.T @ W - np.eye(n)) <= 50 * n * U
+        assert np.linalg.norm(W @ H - A) <= 50 * n * U
+        ctx.set_zolo_control(0, 0)
+        with pytest.raises(B.CSDError) as e:
+            ctx.polar(to_dev(A))
+        assert e.value.status == B.STATUS_NOT_CONVERGED
+        W2, _, info2 = ctx.polar(to_dev(A), allow_not_converged=True)
+        assert info2["status"] == B.STATUS_NOT_CONVERGED and info2["zolo_iters"] == 2
+        assert info2["orth_err"][0] > 50 * n * U
+        assert np.linalg.norm(to_host(W2).T @ to_host(W2) - np.eye(n)) > 50 * n * U
+    finally:
+        ctx.close()
+
+
+def test_polar_converged_input_takes_two_iterations(B):
+    n = 100
+    A, _ = _with_sv(n, np.geomspace(1e-12, 1.0, n), seed=12)
+    W, _, info = B.polar(to_dev(A))
+    assert info["zolo_iters"] == 2 and info["orth_err"][0] <= 50 * n * U
+
+
+# ------------------------------------------------------------------ products
+def _bound(Ah, Bh, Ch, alpha, beta, k):
+    """|C - C_exact| bound of an FP64 product (and of the sliced one, whose
+    error is relative to the row / column maxima)."""
+    absprod = np.abs(Ah) @ np.abs(Bh)
+    rmax = np.max(np.abs(Ah), axis=1)[:, None] if Ah.size else 0.0
+    cmax = np.max(np.abs(Bh), axis=0)[None, :] if Bh.size else 0.0
+    return 4 * (k + 2) * U * (abs(alpha) * absprod + abs(beta) * np.abs(Ch)) + 4 * k * U * abs(alpha) * rmax * cmax
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (5, 3, 7), (128, 64, 64), (300, 200, 517), (129, 65, 2000),
+                                   (1000, 700, 1300)])
+@pytest.mark.parametrize("opA,opB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_gemm_engines_match_definition(B, m, n, k, opA, opB):
+    """csd_gemm on both engines against the definition sum_k a_ik b_kj
+    (numpy FP64 product on the host), ragged shapes, alpha and beta."""
+    rng = np.random.default_rng(m * 7 + n * 3 + k + 10 * opA + 20 * opB)
+    Ah = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-3, 3, (m, 1))
+    Bh = rng.standard_normal((k, n)) * 10.0 ** rng.uniform(-3, 3, (1, n))
+    Ch = rng.standard_normal((m, n))
+    alpha, beta = -0.75, 0.5
+    want = alpha * (Ah @ Bh) + beta * Ch
+    tol = _bound(Ah, Bh, Ch, alpha, beta, k)
+    ctx = B.Context(0)
+    try:
+        for engine in (0, 1):
+            # op(X) = X^T is passed as the stored transpose
+            Ad = to_dev(np.ascontiguousarray(Ah.T)) if opA else to_dev(Ah)
+            Bd = to_dev(np.ascontiguousarray(Bh.T)) if opB else to_dev(Bh)
+            Cd = to_dev(Ch)
+            got = to_host(ctx.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, opA=opA, opB=opB, engine=engine))
+            assert np.all(np.abs(got - want) <= tol), (engine, float(np.max(np.abs(got - want) / tol)))
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("k", [700, 3000])
+def test_tc_int64_write_out_every_drain(B, k):
+    """The tensor-core kernel writes its 64-bit integer sum to C every few
+    drains when K is long (K > 15 360 by default); forcing a write-out at
+    every 128-k drain exercises that path, with beta != 0, on short K."""
+    m, n = 200, 100
+    rng = np.random.default_rng(k)
+    Ah = rng.standard_normal((m, k))
+    Bh = rng.standard_normal((k, n))
+    Ch = rng.standard_normal((m, n))
+    want = 2.0 * (Ah @ Bh) - 3.0 * Ch
+    tol = _bound(Ah, Bh, Ch, 2.0, -3.0, k)
+    ctx = B.Context(0)
+    try:
+        ctx.set_test_hooks(tc_flush_every=1)
+        got = to_host(ctx.gemm(to_dev(Ah), to_dev(Bh), to_dev(Ch), alpha=2.0, beta=-3.0, engine=1))
+        assert np.all(np.abs(got - want) <= tol)
+        ctx.set_test_hooks(tc_flush_every=2)
+        got = to_host(ctx.gemm(to_dev(Ah), to_dev(Bh), to_dev(Ch), alpha=2.0, beta=-3.0, engine=1))
+        assert np.all(np.abs(got - want) <= tol)
+    finally:
+        ctx.close()
+
+
+def test_tc_write_out_every_drain_inside_polar(B):
+    """The same write-out schedule inside a whole polar decomposition, where
+    products use split-K partial outputs and beta C updates."""
+    n = 320
+    A, _ = _with_sv(n, np.geomspace(1e-6, 1.0, n), seed=13)
+    ctx = B.Context(0)
+    try:
+        ctx.set_tensor_cores(True)
+        W0, H0, _ = ctx.polar(to_dev(A))
+        ctx.set_test_hooks(tc_flush_every=1)
+        W1, H1, _ = ctx.polar(to_dev(A))
+        W0, W1, H1 = to_host(W0), to_host(W1), to_host(H1)
+        assert np.linalg.norm(W1.T @ W1 - np.eye(n)) <= 50 * n * U
+        assert np.linalg.norm(W1 @ H1 - A) <= 50 * n * U
+        assert np.linalg.norm(W1 - W0) <= 1e-7
+    finally:
+        ctx.close()
+
+
+# ------------------------------------------------------------------ failure paths
+def test_eig_split_failure_is_reported_after_retries(B):
+    """Host-side injection: every Zolo-eig split attempt is rejected, so the
+    first block retries with each of its six shifted splits and the call
+    returns CSD_ERR_EIG_SPLIT; the next call on the same context works."""
+    n = 150
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((n, n))
+    Bm = X + X.T
+    ctx = B.Context(0)
+    try:
+        ctx.set_test_hooks(flags=B.TEST_REJECT_EIG_SPLITS)
+        with pytest.raises(B.CSDError) as e:
+            ctx.heig(to_dev(Bm))
+        assert e.value.status == 4
+        assert e.value.info["eig_retries"] == 6 and e.value.info["eig_splits"] == 0
+        ctx.set_test_hooks()
+        lam, V, _ = ctx.heig(to_dev(Bm))
+        lam, V = to_host(lam), to_host(V)
+        assert np.max(np.abs(lam - np.linalg.eigvalsh(Bm))) <= 50 * n * U * np.linalg.norm(Bm, 2)
+    finally:
+        ctx.close()
+
+
+def test_tc_wait_that_runs_out_reports_timeout(B):
+    """A bounded wait on a barrier that nothing signals (the kernel's test
+    hook, taken before any copy or MMA is issued) runs out: the product
+    reports CSD_ERR_DEVICE_TIMEOUT, a whole polar decomposition does too, and
+    the next calls on the same context are correct."""
+    m, n, k = 256, 128, 192
+    rng = np.random.default_rng(3)
+    Ah, Bh = rng.standard_normal((m, k)), rng.standard_normal((k, n))
+    ctx = B.Context(0)
+    try:
+        ctx.set_test_hooks(tc_probe_wait=2000)
+        with pytest.raises(B.CSDError) as e:
+            ctx.gemm(to_dev(Ah), to_dev(Bh), engine=1)
+        assert e.value.status == 9
+        ctx.set_tensor_cores(True)
+        A, _ = _with_sv(256, np.geomspace(1e-3, 1.0, 256), seed=14)
+        with pytest.raises(B.CSDError) as e:
+            ctx.polar(to_dev(A))
+        assert e.value.status == 9
+        ctx.set_test_hooks()
+        got = to_host(ctx.gemm(to_dev(Ah), to_dev(Bh), engine=1))
+        assert np.all(np.abs(got - Ah @ Bh) <= _bound(Ah, Bh, np.zeros((m, n)), 1.0, 0.0, k))
+        W, H, _ = ctx.polar(to_dev(A))
+        W = to_host(W)
+        assert np.linalg.norm(W.T @ W - np.eye(256)) <= 50 * 256 * U
+    finally:
+        ctx.close()
