@@ -49,7 +49,7 @@ def parse():
                     help="with --tc 1, also time the FP64-pipe path (same workload, same accuracy checks)")
     ap.add_argument("--config", default="n4096", choices=list(CONFIGS),
                     help="n4096 (headline), n64 (median of 100 after 10), c2048 (complex rank 1536), n8192")
-    ap.add_argument("--mode", default="csd", choices=["csd", "fp64-peak", "oracle-full"],
+    ap.add_argument("--mode", default="csd", choices=["csd", "fp64-peak", "oracle-full", "gemm"],
                     help="fp64-peak: DFMA / mma.sync f64 microbenchmark; oracle-full: the CPU oracle once at full size")
     return ap.parse_args()
 
@@ -60,6 +60,7 @@ CONFIGS = {
     "n64": dict(n=64, cplx=False, rank=None, seed=1, kind="haar"),
     "c2048": dict(n=2048, cplx=True, rank=1536, seed=3, kind="rankdef"),
     "n8192": dict(n=8192, cplx=False, rank=None, seed=4, kind="clustered"),
+    "n1024": dict(n=1024, cplx=False, rank=None, seed=2, kind="clustered"),  # profiling case
 }
 
 
@@ -338,6 +339,42 @@ def run_fp64_peak(args):
           flush=True)
 
 
+def run_gemm(args):
+    """The product kernels alone: C = A B with n x n x n real FP64 operands
+    (N(0,1) entries, 3 x 8 n^2 bytes > L2 at n = 4096) through csd_gemm, on
+    the tensor-core kernel (engine 1) and on the FP64 pipe (engine 0)."""
+    import torch
+    from paper_1804_09002_gb300 import binding as B
+    n = args.n
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(1)
+    A = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g).t()
+    Bm = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g).t()
+    C = torch.zeros(n, n, dtype=torch.float64, device=dev).t()
+    ctx = B.Context(0)
+    res = {}
+    for engine in ([1, 0] if args.compare_fp64 else [1]):
+        for _ in range(args.warmup):
+            ctx.gemm(A, Bm, C, engine=engine)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        for i in range(args.steps):
+            ctx.gemm(A, Bm, C, engine=engine)
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        ms = statistics.median(ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps))
+        fl = 2.0 * n ** 3
+        res["tensor_cores" if engine else "fp64_pipe"] = {
+            "ms": ms, "fp64_equivalent_tflops": fl / ms / 1e9,
+            **({"bf16_slice_tflops": 28 * fl / ms / 1e9,
+                "frac_of_bf16_sustained": 28 * fl / ms / 1e9 / peaks().get("bf16_tflops_sustained", 1719.1)}
+               if engine else {"frac_of_fp64_unit_peak": fl / ms / 1e9 / fp64_alu_peak_tflops()})}
+    err = float(torch.max(torch.abs(C - A @ Bm)))
+    ctx.close()
+    print(json.dumps({"mode": "gemm", "n": n, "steps": args.steps, "max_abs_diff_vs_torch": err, **res}), flush=True)
+
+
 def run_oracle_full(args):
     """The CPU oracle once at the full size of --config (no extrapolation)."""
     import platform
@@ -372,6 +409,9 @@ def main():
         return
     if args.mode == "oracle-full":
         run_oracle_full(args)
+        return
+    if args.mode == "gemm":
+        run_gemm(args)
         return
     import torch
     from paper_1804_09002_gb300 import binding as B

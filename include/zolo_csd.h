@@ -61,7 +61,7 @@ typedef struct {
   int r_terms[4];         /* partial-fraction terms r of each iteration */
   double ell[4];          /* lower end l of [l, 1] entering each iteration */
   int chol_fallback;      /* Cholesky iterations redone in QR form */
-  int alg2_used[2];       /* Algorithm 2 applied to block i */
+  int alg2_used[2];       /* Algorithm 2 applied to block i (2: then the SVD polar fallback) */
   double orth_err[2];     /* ||W_i^* W_i - I||_F of the Zolo-pd factor (polar(): entry 0) */
   double rdiff[2];        /* ||R~_i - R_i||_F / ||R_i||_F (Algorithm 2 check) */
   int eig_splits;         /* Zolo-eig splits performed */
@@ -205,7 +205,8 @@ typedef struct {
    * triangular solves, 15 H, 16 orthogonality check, 17 Zolo-eig,
    * 18 assembly, 19 Algorithm 2, 20 merging of the blocked QR's WY factors,
    * 21 rows of the dense block X in the trailing update of the stacked
-   * [X; sqrt(c) I] QR factorization; site 3 holds the rows below it) */
+   * [X; sqrt(c) I] QR factorization; site 3 holds the rows below it;
+   * 22 csd_polar_backward) */
   long long site_count[24];
   double site_ms[24];
   double site_flops[24];
@@ -229,6 +230,49 @@ int csd_profile_enable(csd_ctx* ctx, int enable);
  * Complex data always uses the FP64 pipe.  Returns 0 or -1 (NULL context). */
 int csd_set_tensor_cores(csd_ctx* ctx, int enable);
 int csd_profile_read(csd_ctx* ctx, csd_profile* out);
+
+/* Fallback of Algorithm 2 (Section 5.1): when ||R~_i - R_i||_F / ||R_i||_F
+ * (the backward error of W_i H~_i, info->rdiff) reaches factor * n * u, the
+ * polar decomposition of A_i is recomputed through the SVD (one-sided
+ * Jacobi, W_i = U V^*, H_i = sym(W_i^* A_i)), which is unconditionally
+ * backward stable, and info->alg2_used[i] = 2.  Default factor 1e3; 0 makes
+ * every block that takes Algorithm 2 use the SVD; a negative factor
+ * disables the fallback, and a block above 1e3 n u then returns
+ * CSD_WARN_ALG2_RCHECK as a warning.  The SVD costs O(n^3) per sweep and
+ * some ten sweeps.  Returns 0, -1 (NULL context) or -2 (NaN). */
+int csd_set_alg2_fallback(csd_ctx* ctx, double factor);
+
+/* Column convention of csd_polar's factors.  The CSD leaves each column
+ * pair (U1, U2, V1)[:, j] free up to a common sign (a common phase when
+ * complex) for distinct angles.  mode 0 (default) keeps what the
+ * algorithm produces; mode 1 scales column j so that the entry of V1[:, j]
+ * of largest magnitude (first such index) is real and positive, which makes
+ * the factors unique for distinct angles and hence differentiable functions
+ * of A (needed by csd_polar_backward's callers that put a loss on U1, U2 or
+ * V1).  Returns 0, -1 (NULL context) or -2. */
+int csd_set_sign_convention(csd_ctx* ctx, int mode);
+
+/* Reverse-mode derivative of csd_polar for a real, full-rank input (the
+ * paper has no derivatives: this is the adjoint of Algorithm 1's steps).
+ * Given the forward's outputs U1, U2, V1 (n x n), theta (length n) and the
+ * gradients gU1, gU2, gV1 (n x n), gtheta (length n) of a scalar loss --
+ * any of them NULL for zero -- writes gA1, gA2 (n x n) = dLoss/dA1, dA2.
+ * It uses that at a partial isometry H1 = V1 diag(cos theta) V1^T and
+ * H2 = V1 diag(sin theta) V1^T (Section 3) and W_i = U_i V1^T, so both polar
+ * adjoints (the Lyapunov equations H dX + dX H = ..., solved by division by
+ * sigma_k + sigma_l) and the eigenvector adjoint of B = H2 - H1 (division by
+ * lambda_l - lambda_k, lambda = sin theta - cos theta) are elementwise in
+ * the basis V1: seven n x n x n products and one elementwise kernel; the
+ * forward's iterates are not needed.  Defined for distinct angles in
+ * (0, pi/2); a repeated angle contributes no eigenvector term (the
+ * eigenvectors are not unique there), an angle at 0 or pi/2 no polar term.
+ * For a loss on U1, U2 or V1, run the forward with csd_set_sign_convention
+ * mode 1.  Pointers may be device or host memory.  dtype must be CSD_F64
+ * (else -2).  Returns 0, -k for invalid argument k, or a CSD_ERR_* code. */
+int csd_polar_backward(csd_ctx* ctx, int dtype, int n, const void* U1, int ldu1, const void* U2, int ldu2,
+                       const void* V1, int ldv1, const double* theta, const void* gU1, int ldgu1, const void* gU2,
+                       int ldgu2, const void* gV1, int ldgv1, const double* gtheta, void* gA1, int ldga1, void* gA2,
+                       int ldga2, csd_info* info);
 
 /* Zolo-pd iteration control of polar() (Section 5).
  *   max_extra_passes (0..4, default 1): Section 5's two iterations on

@@ -58,7 +58,7 @@ class csd_profile(ctypes.Structure):
 
     SITES = ["other", "qr_W", "qr_W2", "qr_update", "formq_W", "formq_W2", "formq_update", "zolo_combine",
              "gram", "chol_row", "chol_trailing", "trsm_f_update", "trsm_f_diag", "trsm_b_update",
-             "trsm_b_diag", "H", "orth", "eig", "assembly", "alg2", "tmerge", "qr_update_x"]
+             "trsm_b_diag", "H", "orth", "eig", "assembly", "alg2", "tmerge", "qr_update_x", "grad"]
 
 
 def _load():
@@ -90,6 +90,10 @@ def _load():
     lib.csd_set_test_hooks.argtypes = [vp, ctypes.c_uint, ctypes.c_longlong, ci]
     lib.csd_gemm.argtypes = [vp, ci, ci, ci, ci, ci, cd, vp, ci, vp, ci, cd, vp, ci, ci]
     lib.csd_fp64_peak.argtypes = [ci, ci, ctypes.POINTER(cd), ctypes.POINTER(cd)]
+    lib.csd_set_sign_convention.argtypes = [vp, ci]
+    lib.csd_set_alg2_fallback.argtypes = [vp, cd]
+    lib.csd_polar_backward.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, vp, vp, ci, vp, ci, vp, ci, vp, vp, ci,
+                                       vp, ci, ctypes.POINTER(csd_info)]
     lib.csd_launch_count.argtypes = []
     lib.csd_launch_count.restype = ctypes.c_longlong
     lib.csd_status_str.argtypes = [ci]
@@ -97,7 +101,8 @@ def _load():
     for f in ("csd_create", "csd_set_stream", "csd_destroy", "csd_polar", "polar", "heig", "zolo_coeffs",
               "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc", "csd_set_tensor_cores",
               "csd_set_theta_mode", "csd_complete_v2", "csd_polar_rect", "csd_set_zolo_control",
-              "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak"):
+              "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak", "csd_set_sign_convention",
+              "csd_polar_backward", "csd_set_alg2_fallback"):
         getattr(lib, f).restype = ci
     return lib
 
@@ -107,7 +112,8 @@ lib = _load()
 EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes", "csd_polar", "polar", "heig",
             "zolo_coeffs", "zolo_plan", "csd_status_str", "csd_profile_enable", "csd_profile_read",
             "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores", "csd_set_theta_mode", "csd_complete_v2",
-            "csd_polar_rect", "csd_set_zolo_control", "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak"]
+            "csd_polar_rect", "csd_set_zolo_control", "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak",
+            "csd_set_sign_convention", "csd_polar_backward", "csd_set_alg2_fallback"]
 
 STATUS_NOT_CONVERGED = 2
 TEST_REJECT_EIG_SPLITS = 1
@@ -264,6 +270,57 @@ class Context:
         st = lib.csd_set_theta_mode(self._h, int(mode))
         if st != 0:
             raise CSDError(st, "csd_set_theta_mode")
+
+    def set_alg2_fallback(self, factor=1e3):
+        """SVD polar fallback of Algorithm 2 when ||R~ - R|| / ||R|| reaches
+        factor n u (0: always; negative: never, warn instead)."""
+        st = lib.csd_set_alg2_fallback(self._h, float(factor))
+        if st != 0:
+            raise CSDError(st, "csd_set_alg2_fallback")
+
+    def set_sign_convention(self, mode=1):
+        """1: each column of V1 (with U1, U2) has its largest-magnitude entry
+        real positive, so the factors are unique for distinct angles."""
+        st = lib.csd_set_sign_convention(self._h, int(mode))
+        if st != 0:
+            raise CSDError(st, "csd_set_sign_convention")
+
+    def csd_backward(self, U1, U2, V1, theta, gU1=None, gU2=None, gV1=None, gtheta=None):
+        """(gA1, gA2) of a loss with gradients gU1, gU2, gV1, gtheta (None =
+        zero) at the outputs of csd_polar (real, full rank)."""
+        U1, p1, l1 = _colmajor(U1)
+        U2, p2, l2 = _colmajor(U2)
+        V1, pv, lv = _colmajor(V1)
+        n = V1.shape[1]
+        if _dtype_code(V1) != CSD_F64:
+            raise TypeError("csd_backward is defined for real float64 factors")
+
+        def opt(x):
+            if x is None:
+                return None, None, n
+            x, p, ld = _colmajor(x)
+            return x, p, ld
+
+        def vec(x):
+            if x is None:
+                return None, None
+            x = x.contiguous() if _is_torch(x) else np.ascontiguousarray(x, dtype=np.float64)
+            return x, _ptr(x)
+
+        gU1, pg1, lg1 = opt(gU1)
+        gU2, pg2, lg2 = opt(gU2)
+        gV1, pgv, lgv = opt(gV1)
+        theta, pth = vec(theta)
+        gtheta, pgt = vec(gtheta)
+        gA1 = _empty_like2(V1, n, n)
+        gA2 = _empty_like2(V1, n, n)
+        info = csd_info()
+        self._bind_stream(V1)
+        st = lib.csd_polar_backward(self._h, CSD_F64, n, p1, l1, p2, l2, pv, lv, pth, pg1, lg1, pg2, lg2, pgv, lgv,
+                                    pgt, _ptr(gA1), n, _ptr(gA2), n, ctypes.byref(info))
+        if st != 0:
+            raise CSDError(st, "csd_polar_backward", info.as_dict())
+        return gA1, gA2
 
     def set_zolo_control(self, max_extra_passes=1, stop_after=0):
         """polar(): further plan passes when the iterate has not converged

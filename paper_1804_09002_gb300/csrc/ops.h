@@ -24,7 +24,7 @@ constexpr int MAX_SUM = 16;
 enum GemmSite {
   GS_OTHER = 0, GS_QR_W, GS_QR_W2, GS_QR_UPD, GS_FQ_W, GS_FQ_W2, GS_FQ_UPD, GS_ZOLO_COMBINE, GS_GRAM,
   GS_CHOL_ROW, GS_CHOL_TRAIL, GS_TRSM_F_UPD, GS_TRSM_F_DIAG, GS_TRSM_B_UPD, GS_TRSM_B_DIAG, GS_H, GS_ORTH,
-  GS_EIG, GS_ASSEMBLY, GS_ALG2, GS_TMERGE, GS_QR_UPD_X, GS_SITES
+  GS_EIG, GS_ASSEMBLY, GS_ALG2, GS_TMERGE, GS_QR_UPD_X, GS_GRAD, GS_SITES
 };
 
 template <class T>

@@ -509,8 +509,20 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     d2h(cx, cx.hs.d, sc + 8, sizeof(double));
     const double rd = std::sqrt(cx.hs.d[0]) / std::max(std::sqrt(fro / 2.0), 1e-300);
     if (info) { info->alg2_used[i] = 1; info->rdiff[i] = rd; }
-    if (rd > 1e3 * n * U_ROUND) status = CSD_WARN_ALG2_RCHECK;
     ar.release(mk);
+    if (rd > 1e3 * n * U_ROUND || (cx.alg2_svd_factor >= 0.0 && rd >= cx.alg2_svd_factor * n * U_ROUND)) {
+      if (cx.alg2_svd_factor < 0.0) {
+        status = CSD_WARN_ALG2_RCHECK;
+      } else {
+        // Section 5.1: ||R~ - R|| not O(u), so W_i H_i is not a backward
+        // stable polar decomposition of A_i; take the polar decomposition
+        // from the SVD instead (W_i = U V^*, H_i = sym(W_i^* A_i))
+        svd_polar<T>(cx, ar, n, Apk + i * nn, n, W + i * nn, n);
+        gemm1<T>(st, OP_C, OP_N, n, n, n, one, W + i * nn, n, Apk + i * nn, n, zer, H + i * nn, n, 0, 0, GS_H);
+        symmetrize<T>(st, n, H + i * nn, n, 0, H + i * nn, n, 0, 1);
+        if (info) info->alg2_used[i] = 2;
+      }
+    }
   };
   // full rank: Algorithm 2 where W_i is not orthonormal
   const double orth_tol = 50.0 * n * U_ROUND;
@@ -609,6 +621,7 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
     gather_cols<T>(st, n, rk, Ut, n, perm, U1, ldu1);
     gather_cols<T>(st, n, rk, Ut + nn, n, perm, U2, ldu2);
     gather_cols<T>(st, n, rk, Vr, n, perm, V1, ldv1);
+    if (cx.sign_mode == 1) canonical_signs<T>(st, n, n, n, rk, V1, ldv1, U1, ldu1, U2, ldu2);
   }
   if (rk < n) {
     zero_tail_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, rk, theta);
@@ -1118,6 +1131,32 @@ int complete_v2_typed(csd_ctx* ctx, int n, const void* A3, int lda3, const void*
   });
 }
 
+int backward_typed(csd_ctx* ctx, int n, const void* U1, int ldu1, const void* U2, int ldu2, const void* V1, int ldv1,
+                   const double* theta, const void* gU1, int ldgu1, const void* gU2, int ldgu2, const void* gV1,
+                   int ldgv1, const double* gtheta, void* gA1, int ldga1, void* gA2, int ldga2, csd_info* info) {
+  Ctx& cx = ctx->cx;
+  const size_t need = (size_t)16 * n * n * sizeof(double) + ((size_t)1 << 20);
+  return run_with_ws(cx, need, info, [&](Arena& ar) -> int {
+    Mat<double> u1 = view_in<double>(cx, ar, U1, ldu1, n, n);
+    Mat<double> u2 = view_in<double>(cx, ar, U2, ldu2, n, n);
+    Mat<double> v1 = view_in<double>(cx, ar, V1, ldv1, n, n);
+    Mat<double> th = view_in<double>(cx, ar, theta, n, n, 1);
+    Mat<double> gu1, gu2, gv1, gth;
+    if (gU1) gu1 = view_in<double>(cx, ar, gU1, ldgu1, n, n);
+    if (gU2) gu2 = view_in<double>(cx, ar, gU2, ldgu2, n, n);
+    if (gV1) gv1 = view_in<double>(cx, ar, gV1, ldgv1, n, n);
+    if (gtheta) gth = view_in<double>(cx, ar, gtheta, n, n, 1);
+    Mat<double> ga1 = view_out<double>(ar, gA1, ldga1, n, n);
+    Mat<double> ga2 = view_out<double>(ar, gA2, ldga2, n, n);
+    int st = csd_backward_impl(cx, ar, n, u1.d, u1.ld, u2.d, u2.ld, v1.d, v1.ld, th.d, gu1.d, gu1.ld, gu2.d, gu2.ld,
+                               gv1.d, gv1.ld, gth.d, ga1.d, ga1.ld, ga2.d, ga2.ld);
+    copy_out(cx, ga1, n, n);
+    copy_out(cx, ga2, n, n);
+    ZCSD_CUDA(cudaStreamSynchronize(cx.stream));
+    return st;
+  });
+}
+
 // C = alpha op(A) op(B) + beta C on the FP64 pipe (engine 0) or the
 // tensor-core kernel (engine 1, any shape).
 int gemm_typed(csd_ctx* ctx, int opA, int opB, int m, int n, int k, double alpha, const double* A, int lda,
@@ -1147,6 +1186,46 @@ int gemm_typed(csd_ctx* ctx, int opA, int opB, int m, int n, int k, double alpha
 }  // namespace
 
 extern "C" {
+
+int csd_set_alg2_fallback(csd_ctx* ctx, double factor) {
+  if (!ctx) return -1;
+  if (!(factor == factor)) return -2;
+  ctx->cx.alg2_svd_factor = factor;
+  return CSD_OK;
+}
+
+int csd_set_sign_convention(csd_ctx* ctx, int mode) {
+  if (!ctx) return -1;
+  if (mode != 0 && mode != 1) return -2;
+  ctx->cx.sign_mode = mode;
+  return CSD_OK;
+}
+
+int csd_polar_backward(csd_ctx* ctx, int dtype, int n, const void* U1, int ldu1, const void* U2, int ldu2,
+                       const void* V1, int ldv1, const double* theta, const void* gU1, int ldgu1, const void* gU2,
+                       int ldgu2, const void* gV1, int ldgv1, const double* gtheta, void* gA1, int ldga1, void* gA2,
+                       int ldga2, csd_info* info) {
+  if (!ctx) return -1;
+  if (dtype != CSD_F64) return -2;
+  if (n < 1) return -3;
+  if (!U1) return -4;
+  if (ldu1 < n) return -5;
+  if (!U2) return -6;
+  if (ldu2 < n) return -7;
+  if (!V1) return -8;
+  if (ldv1 < n) return -9;
+  if (!theta) return -10;
+  if (gU1 && ldgu1 < n) return -12;
+  if (gU2 && ldgu2 < n) return -14;
+  if (gV1 && ldgv1 < n) return -16;
+  if (!gA1) return -18;
+  if (ldga1 < n) return -19;
+  if (!gA2) return -20;
+  if (ldga2 < n) return -21;
+  if (info) std::memset(info, 0, sizeof(csd_info));
+  return backward_typed(ctx, n, U1, ldu1, U2, ldu2, V1, ldv1, theta, gU1, ldgu1, gU2, ldgu2, gV1, ldgv1, gtheta, gA1,
+                        ldga1, gA2, ldga2, info);
+}
 
 int csd_set_zolo_control(csd_ctx* ctx, int max_extra_passes, int stop_after) {
   if (!ctx) return -1;

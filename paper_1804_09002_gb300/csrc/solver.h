@@ -38,6 +38,8 @@ struct Ctx {
   long long tc_probe_wait = 0;  // tensor-core kernel: polls of a barrier nothing signals (0 = none)
   int tc_flush_every = 0;       // tensor-core kernel: drains between int64 write-outs (0 = default)
   bool force_tc_err = false;    // the running call needs the tensor-core error flag (csd_gemm)
+  int sign_mode = 0;            // 1: canonical column signs of U1, U2, V1 (csd_set_sign_convention)
+  double alg2_svd_factor = 1e3;  // SVD polar fallback when ||R~ - R|| / ||R|| > factor n u (< 0: never)
 };
 
 // Host-side fault injection for the failure-path tests.
@@ -65,6 +67,24 @@ void d2h(Ctx& cx, void* dst, const void* src, size_t bytes);
 // stop_after > 0 stops after that many iterations (the iterate X_k).
 template <class T>
 void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after = 0);
+
+// Columns of V (and of U1, U2) scaled by the inverse phase of V's entry of
+// largest magnitude (real: made positive), columns 0..ncols-1.
+template <class T>
+void canonical_signs(cudaStream_t st, int m1, int m2, int n, int ncols, T* V, int ldv, T* U1, int ldu1, T* U2,
+                     int ldu2);
+
+// W = U V^* from the one-sided Jacobi SVD A = U Sigma V^* (svd.cu): the
+// SVD-based polar factor of Section 5.1's fallback.  A and W n x n.
+template <class T>
+void svd_polar(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* W, int ldw);
+
+// Reverse-mode derivative of the full-rank real CSD from its outputs
+// (grad.cu); gradient inputs may be null (zero).
+int csd_backward_impl(Ctx& cx, Arena& ar, int n, const double* U1, int ldu1, const double* U2, int ldu2,
+                      const double* V, int ldv, const double* theta, const double* gU1, int ldgu1, const double* gU2,
+                      int ldgu2, const double* gV, int ldgv, const double* gtheta, double* gA1, int ldga1, double* gA2,
+                      int ldga2);
 
 // The polar() entry point on an arena the caller provides (also used by the
 // allocation-free entry point).  Returns a CSD_* status.

@@ -9,25 +9,40 @@
 // column j of op(B) with eb_j.  Each slice q~_s = q_s 2^-8(s-1) is exact in
 // BF16.  Then
 //   op(A) op(B) = 2^(ea_i + eb_j - 16) sum_{s+t <= 8} A~_s B~_t  (+ O(2^-56) x row/col maxima),
-// and every BF16 x BF16 product is exact in FP32.  The 28 slice products are
-// issued as tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM) into six
-// accumulators by g = s + t: g = 2, 3, 4, 5, 6 and "g >= 7".  For g <= 6 the
-// integer sums of 128 consecutive k stay below 2^24 (|q_1| <= 256, |q_s| <=
-// 128 for s >= 2), so those accumulators are exact and are added into FP64
-// registers every 128 k.  The g >= 7 accumulator holds terms below 2^-40 of
-// the result; its FP32 rounding is far below FP64 rounding, and it is added
-// at the end.  The FP64 sum is then scaled by 2^(ea_i + eb_j - 16).
+// and every BF16 x BF16 product is exact in FP32.  The 28 slice products
+// accumulate by g = s + t into seven FP32 accumulators in TMEM (g = 2..8).
+// For g <= 6 the integer sums of 128 consecutive k stay below 2^24
+// (|q_1| <= 256, |q_s| <= 128 for s >= 2), so those accumulators are exact;
+// every 128 k they are converted to a 64-bit fixed-point sum kept in
+// registers and zeroed.  Groups 7 and 8 hold terms below 2^-40 of the result
+// and are read once at the end.
 //
-// Layout: a CTA computes a 128 x 64 FP64 output tile with 128 threads and
-// 6 x 64 TMEM columns (512 allocated).  Per
-// 64-wide k chunk it stages 7 A slices (128 x 64) and 7 B slices (64 x 64) in
-// shared memory as K-major 8 x 16-byte core matrices (no swizzle), thread 0
-// issues the 28 x 4 MMAs (M = 128, N = 64, K = 16), completion is signalled
-// through tcgen05.commit on an mbarrier (bounded wait), and the four warps
-// read their 32 TMEM lanes each with tcgen05.ld.
+// Kernel organisation (one CTA per SM, persistent over output tiles):
+//  * warp 0, one lane: producer.  Per 16-wide k stage it loads the 7 A slices
+//    (128 rows) and the 7 B slices (64 rows) with one cp.async.bulk.tensor
+//    (TMA) box each into a 5-deep ring of stages (full/empty mbarriers).
+//    The slices are stored in global memory as [term][k/8][slice][row][8 k],
+//    so each box lands as K-major 8 x 16-byte core matrices with the rows of
+//    all 7 slices consecutive;
+//  * warp 1, one lane: MMA issuer.  Because the B rows of slices t = 1..7
+//    are consecutive and accumulator g sits at TMEM columns 64 (g - 2), the
+//    products of A slice s with every B slice t <= 8 - s form ONE product of
+//    N = 64 (8 - s) columns into accumulators g = s + 1 .. 8: ten MMAs
+//    (M = 128, N <= 256, K = 16) per stage instead of 28;
+//  * warps 2..17: epilogue.  Warp w reads TMEM lanes 32 (w mod 4) .. (its
+//    output rows) and one quarter of the 64 columns; it drains the exact
+//    accumulators every 128 k, and at the end of a tile builds the FP64
+//    result from the int64 sum and writes C.
+// Every wait is bounded; a wait that runs out sets the CTA's abort flag and
+// the device error flag, every role leaves its loop, the producer waits
+// (bounded) for its copies in flight and the MMA issuer for its MMAs before
+// TMEM is released, and the outputs of unfinished tiles are NaN.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <climits>
+#include <mutex>
 
 #include "tc_gemm.h"
 
@@ -35,19 +50,27 @@ namespace zcsd {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 32, TC_S = 7;  // TC_BK: k per pipeline stage
-constexpr int TC_KALIGN = 64;  // slices are padded along k to the slicing tile
-constexpr int TC_THREADS = 256;  // warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..
-constexpr int TC_CPT = TC_BN / 2;  // output columns per thread
-constexpr int TC_NACC = 6;          // accumulators: g = 2..6 exact, g >= 7
-constexpr int TC_TMEM_COLS = 512;   // power of two >= TC_NACC * TC_BN + 2 * TC_BN
-constexpr int TC_ILO = TC_NACC * TC_BN, TC_IHI = TC_ILO + TC_BN;  // fixed-point sum (low / high words)
-constexpr int TC_SLICE_A_BYTES = TC_BM * TC_BK * 2;  // 8 KiB
-constexpr int TC_SLICE_B_BYTES = TC_BN * TC_BK * 2;  // 4 KiB
-constexpr int TC_STAGE_A = TC_S * TC_SLICE_A_BYTES, TC_STAGE_B = TC_S * TC_SLICE_B_BYTES;
-constexpr int TC_SMEM = 2 * (TC_STAGE_A + TC_STAGE_B) + 1024;  // two stages
+constexpr int TC_BM = 128, TC_BN = 64, TC_S = 7;
+constexpr int TC_KS = 16;            // k per pipeline stage (one MMA K)
+constexpr int TC_NSTAGE = 5;         // depth of the stage ring
+constexpr int TC_KALIGN = 64;        // slices are padded along k to the slicing tile
+constexpr int TC_NACC = 7;           // accumulators g = 2..8
+constexpr int TC_NEXACT = 5;         // g = 2..6: drained exactly every 128 k
+constexpr int TC_DRAIN_STAGES = 128 / TC_KS;
+constexpr int TC_EPI_WARPS = 16;
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
+constexpr int TC_CPT = TC_BN / 4;    // output columns per epilogue thread (16)
+constexpr int TC_TMEM_COLS = 512;    // power of two >= 7 x 64
+constexpr int TC_A_STAGE = TC_S * TC_BM * TC_KS * 2;   // 28 KiB
+constexpr int TC_B_STAGE = TC_S * TC_BN * TC_KS * 2;   // 14 KiB
+constexpr int TC_STAGE = TC_A_STAGE + TC_B_STAGE;
+constexpr int TC_SMEM = TC_NSTAGE * TC_STAGE + 1024;
+constexpr uint32_t TC_LBO_A = TC_S * TC_BM * 16;       // next 8-wide k group
+constexpr uint32_t TC_LBO_B = TC_S * TC_BN * 16;
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 constexpr int TC_MAX_DRAINS = 120;  // intermediate drains before the int64 sum is written out
+static_assert(TC_SMEM <= 227 * 1024, "stage ring exceeds shared memory");
+static_assert(TC_NACC * TC_BN <= TC_TMEM_COLS, "accumulators exceed TMEM");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -70,68 +93,79 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc) {
   asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      "l"(ad), "l"(bd), "r"(idesc));
 }
 
-// 16-byte global -> shared copy without a register round trip (both addresses
-// are 16-byte aligned: slice rows are padded to multiples of 64 elements)
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t phase, long long limit = TC_WAIT_LIMIT) {
-  uint32_t done = 0;
-  for (long long it = 0; it < limit && !done; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(phase));
-  }
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(parity)
+      : "memory");
   return done != 0;
 }
 
-// 16 FP32 columns of this thread's TMEM lane starting at column `col`
+// Bounded wait for the phase of `parity`; gives up after `limit` polls or
+// as soon as the CTA's abort flag is set.  Returns true on completion.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_flag,
+                                          long long limit = TC_WAIT_LIMIT) {
+  for (long long it = 0; it < limit; ++it) {
+    if (mbar_try(addr, parity)) return true;
+    if (abort_flag && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+
+// 5-D tiled TMA load into shared memory, completion counted on `mbar`
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                          uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t addr, const uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 16 zero columns of this thread's TMEM lane starting at `addr`
+__device__ __forceinline__ void tmem_zero16(uint32_t addr) {
+  const uint32_t z = 0u;
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(addr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
-  asm volatile("tcgen05.wait::st.sync.aligned;");
-}
-
-// The fixed-point sum I = 2^32 sum_{g=2..6} (group g) of 16 columns lives in
-// TMEM (low words at column TC_ILO, high words at TC_IHI) between drains, so
-// no registers stay live across the k loop.
-__device__ __forceinline__ void ifix_load16(uint32_t tmem_row, int c, long long (&I)[16]) {
-  uint32_t lo[16], hi[16];
-  tmem_ld16(tmem_row + (uint32_t)(TC_ILO + c), lo);
-  tmem_ld16(tmem_row + (uint32_t)(TC_IHI + c), hi);
-#pragma unroll
-  for (int j = 0; j < 16; ++j) I[j] = (long long)(((unsigned long long)hi[j] << 32) | lo[j]);
-}
-
-__device__ __forceinline__ void ifix_store16(uint32_t tmem_row, int c, const long long (&I)[16]) {
-  uint32_t lo[16], hi[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    lo[j] = (uint32_t)(unsigned long long)I[j];
-    hi[j] = (uint32_t)((unsigned long long)I[j] >> 32);
-  }
-  tmem_st16(tmem_row + (uint32_t)(TC_ILO + c), lo);
-  tmem_st16(tmem_row + (uint32_t)(TC_IHI + c), hi);
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(addr),
+      "r"(z)
+      : "memory");
 }
 
 // Exact groups g = 2..6 (accumulators a = g - 2) into I: accumulator a holds
@@ -139,14 +173,14 @@ __device__ __forceinline__ void ifix_store16(uint32_t tmem_row, int c, const lon
 // x 2^8a and a conversion give that integer exactly, which enters I shifted
 // left by 8 (4 - a).  Integer arithmetic only: the FP64 pipe runs 2 lanes per
 // clock per SM.
-__device__ __forceinline__ void drain_exact16(uint32_t tmem_row, int c, long long (&I)[16]) {
+__device__ __forceinline__ void drain_exact(uint32_t tmem_row, long long (&I)[TC_CPT]) {
 #pragma unroll
-  for (int a = 0; a < TC_NACC - 1; ++a) {
-    uint32_t r[16];
-    tmem_ld16(tmem_row + (uint32_t)(a * TC_BN + c), r);
+  for (int a = 0; a < TC_NEXACT; ++a) {
+    uint32_t r[TC_CPT];
+    tmem_ld16(tmem_row + (uint32_t)(a * TC_BN), r);
     const float up = __int_as_float((127 + 8 * a) << 23);  // 2^(8a)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) I[j] += (long long)__float2int_rn(__uint_as_float(r[j]) * up) << (8 * (4 - a));
+    for (int j = 0; j < TC_CPT; ++j) I[j] += (long long)__float2int_rn(__uint_as_float(r[j]) * up) << (8 * (4 - a));
   }
 }
 
@@ -186,12 +220,10 @@ __device__ __forceinline__ double scale_out(double d, int e, double alpha, bool 
 
 struct TcArgs {
   int m, n, kpad, nsum, batch;
-  const __nv_bfloat16* Asl;  // [batch][nsum][S][mpad][kpad]
-  const __nv_bfloat16* Bsl;  // [batch][nsum][S][npad][kpad]
   const int* ea;             // [batch][mpad]
   const int* eb;             // [batch][npad]
-  long long sAsl, sBsl;      // elements per (batch, term) slice set
-  int mpad, npad;
+  int mpad, npad;            // row pitch of the A / B slices and exponents
+  int tiles_n;               // output tiles along n
   int kb_flags;              // K_FROM_COL / K_FROM_ROW / K_TO_COL / K_TO_ROW
   int ksplit;                // split-K parts: problem b, part s writes C_{b * ksplit + s}
   int uplo;
@@ -203,39 +235,62 @@ struct TcArgs {
   long long probe_wait;    // > 0: first poll a barrier nothing signals (timeout-path tests)
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1 KiB alignment of the operand area
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + 2 * TC_STAGE_A;
-  __shared__ __align__(8) uint64_t mbar[3];  // MMA completion of the stage in buffer 0 / 1; [2]: probe
-  __shared__ uint32_t tmem_slot;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int z = blockIdx.z;
-  const int b = z / g.ksplit, kpart = z % g.ksplit;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-  if (g.uplo == 1 && m0 > n0 + TC_BN - 1) return;
-  if (g.uplo == 2 && n0 > m0 + TC_BM - 1) return;
+// One output tile of one problem (and split-K part) with its k range.
+struct TcItem {
+  int m0, n0, b, kpart, kb, nst;  // nst: 16-wide k stages per term
+  bool skip;
+};
+
+__device__ __forceinline__ TcItem tc_item(const TcArgs& g, int it) {
+  TcItem t;
+  const int tm = g.mpad / TC_BM, tn = g.tiles_n;
+  const int mt = it % tm, nt = (it / tm) % tn, z = it / (tm * tn);
+  t.b = z / g.ksplit;
+  t.kpart = z % g.ksplit;
+  t.m0 = mt * TC_BM;
+  t.n0 = nt * TC_BN;
+  t.skip = (g.uplo == 1 && t.m0 > t.n0 + TC_BN - 1) || (g.uplo == 2 && t.n0 > t.m0 + TC_BM - 1);
   int kb = 0, ke = g.kpad;
-  if (g.ksplit > 1) {  // split-K: part kpart takes one 64-aligned K range
-    const int kc = ceil_div_d(ceil_div_d(g.kpad, g.ksplit), TC_BK) * TC_BK;
-    kb = kpart * kc;
+  if (g.ksplit > 1) {  // split-K: part kpart takes one TC_KS-aligned K range
+    const int kc = ceil_div_d(ceil_div_d(g.kpad, g.ksplit), TC_KS) * TC_KS;
+    kb = t.kpart * kc;
     ke = min(g.kpad, kb + kc);
   }
-  if (g.kb_flags & K_FROM_COL) kb = max(kb, n0);
-  if (g.kb_flags & K_FROM_ROW) kb = max(kb, m0);
-  if (g.kb_flags & K_TO_COL) ke = min(ke, n0 + TC_BN);
-  if (g.kb_flags & K_TO_ROW) ke = min(ke, m0 + TC_BM);
-  kb = (kb / TC_BK) * TC_BK;
+  if (g.kb_flags & K_FROM_COL) kb = max(kb, t.n0);
+  if (g.kb_flags & K_FROM_ROW) kb = max(kb, t.m0);
+  if (g.kb_flags & K_TO_COL) ke = min(ke, t.n0 + TC_BN);
+  if (g.kb_flags & K_TO_ROW) ke = min(ke, t.m0 + TC_BM);
+  kb = (kb / TC_KS) * TC_KS;
+  t.kb = kb;
+  t.nst = ke > kb ? (ke - kb + TC_KS - 1) / TC_KS : 0;
+  return t;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[TC_NSTAGE], empty_bar[TC_NSTAGE];
+  __shared__ __align__(8) uint64_t accf_bar, acce_bar, done_bar, probe_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  volatile int* abort_v = &abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles = (g.mpad / TC_BM) * g.tiles_n * g.batch * g.ksplit;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[2])), "r"(1));
+    for (int i = 0; i < TC_NSTAGE; ++i) {
+      mbar_init(smem_u32(&full_bar[i]), 1);
+      mbar_init(smem_u32(&empty_bar[i]), 1);
+    }
+    mbar_init(smem_u32(&accf_bar), 1);
+    mbar_init(smem_u32(&acce_bar), 32 * TC_EPI_WARPS);
+    mbar_init(smem_u32(&done_bar), 1);
+    mbar_init(smem_u32(&probe_bar), 1);
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(TC_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -244,205 +299,214 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * TC_CPT);
-  const int cbase = n0 + (warp >> 2) * TC_CPT;  // first output column of this thread
-  constexpr uint32_t IDESC = idesc_bf16(TC_BM, TC_BN);
-  const uint32_t mbar_addr[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
-
-  {  // fixed-point sum I = 0
-    const long long z16[16] = {};
-#pragma unroll
-    for (int c = 0; c < TC_CPT; c += 16) ifix_store16(tmem_row, c, z16);
-  }
-  bool ok = true;
-  if (g.probe_wait > 0) {
-    // test hook: a bounded wait on a barrier that nothing signals, before
-    // any copy or MMA is issued; it runs out and the launch takes the
-    // timeout path (NaN outputs, error flag)
-    ok = __syncthreads_and(tid != 0 || mbar_wait(smem_u32(&mbar[2]), 0u, g.probe_wait)) != 0;
-  }
-  // accumulator a at TMEM columns [64 a, 64 a + 64): a = g - 2 for g <= 6, a = 5 for g >= 7
-  uint32_t filled = 0;  // bit a set: accumulator a holds data since its last drain
-  int chunks_since_drain = 0, nchunks = 0, ndrain = 0;
-  bool flushed = false;  // a partial sum was already written to C
-  const int row = m0 + (warp & 3) * 32 + lane;
-  const int ea = row < g.m ? g.ea[(long long)b * g.mpad + row] : 0;
-  const bool aunit = g.alpha == 1.0 || g.alpha == -1.0;
-  const unsigned long long asgn = (aunit && g.alpha < 0.0) ? (1ull << 63) : 0ull;
-  double* C = g.C + (long long)z * g.sC;
-  const double* Cin = (g.Cin && kpart == 0 && g.beta != 0.0) ? g.Cin + (long long)(b / g.bdivC) * g.sCin : nullptr;
-
-  // stages q = 0 .. Q-1: term js = q / nst, k range [kb + 32 (q % nst), +32);
-  // the slices of stage q + 1 load (cp.async) into the other buffer while
-  // the MMAs of stage q run; a buffer is refilled once the MMAs that read it
-  // have signalled their mbarrier
-  const int nst = ke > kb ? (ke - kb + TC_BK - 1) / TC_BK : 0;
-  const int Q = g.nsum * nst;
-  auto load_stage = [&](int q, int buf) {
-    const int js = q / nst, k0 = kb + (q % nst) * TC_BK;
-    const __nv_bfloat16* Ab = g.Asl + ((long long)b * g.nsum + js) * g.sAsl;
-    const __nv_bfloat16* Bb = g.Bsl + ((long long)b * g.nsum + js) * g.sBsl;
-    unsigned char* dA = sA + buf * TC_STAGE_A;
-    unsigned char* dB = sB + buf * TC_STAGE_B;
-    // vector v = (slice, row, k/8): 16 bytes of 8 consecutive k, placed as
-    // K-major 8 x 16-byte core matrices
-    for (int v = tid; v < TC_S * TC_BM * (TC_BK / 8); v += TC_THREADS) {
-      const int sl = v / (TC_BM * (TC_BK / 8)), rem = v % (TC_BM * (TC_BK / 8));
-      const int r = rem / (TC_BK / 8), kq = rem % (TC_BK / 8);
-      cp_async16(dA + sl * TC_SLICE_A_BYTES + ((r >> 3) * (TC_BK / 8) + kq) * 128 + (r & 7) * 16,
-                 Ab + (long long)sl * g.mpad * g.kpad + (long long)(m0 + r) * g.kpad + k0 + kq * 8);
-    }
-    for (int v = tid; v < TC_S * TC_BN * (TC_BK / 8); v += TC_THREADS) {
-      const int sl = v / (TC_BN * (TC_BK / 8)), rem = v % (TC_BN * (TC_BK / 8));
-      const int r = rem / (TC_BK / 8), kq = rem % (TC_BK / 8);
-      cp_async16(dB + sl * TC_SLICE_B_BYTES + ((r >> 3) * (TC_BK / 8) + kq) * 128 + (r & 7) * 16,
-                 Bb + (long long)sl * g.npad * g.kpad + (long long)(n0 + r) * g.kpad + k0 + kq * 8);
-    }
-    asm volatile("cp.async.commit_group;");
+  auto fail = [&]() {
+    *abort_v = 1;
+    atomicExch(g.err, 1);
   };
-  uint32_t ph[2] = {0u, 0u};
-  bool pend[2] = {false, false};
-  // wait (bounded, uniform over the CTA) for the MMAs committed on buffer bf
-  auto wait_buf = [&](int bf) {
-    if (!pend[bf]) return;
-    ok = __syncthreads_and(ok && mbar_wait(mbar_addr[bf], ph[bf])) != 0;
-    ph[bf] ^= 1u;
-    pend[bf] = false;
-  };
-  if (Q > 0) load_stage(0, 0);
-  for (int q = 0; q < Q && ok; ++q) {
-    const int buf = q & 1;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");  // stage q (the only group in flight)
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(sA + buf * TC_STAGE_A), b0 = smem_u32(sB + buf * TC_STAGE_B);
-      for (int s1 = 1; s1 <= TC_S; ++s1)
-        for (int t1 = 1; t1 <= TC_S + 1 - s1; ++t1) {
-          const int gi = s1 + t1;
-          const int a = gi <= 6 ? gi - 2 : 5;
-#pragma unroll
-          for (int ks = 0; ks < TC_BK / 16; ++ks) {
-            const uint64_t ad = smem_desc(a0 + (s1 - 1) * TC_SLICE_A_BYTES + ks * 256, 128, (TC_BK / 8) * 128);
-            const uint64_t bd = smem_desc(b0 + (t1 - 1) * TC_SLICE_B_BYTES + ks * 256, 128, (TC_BK / 8) * 128);
-            const uint32_t accum = (filled >> a) & 1u;
-            mma_bf16(tmem + (uint32_t)(a * TC_BN), ad, bd, IDESC, accum);
-            filled |= (1u << a);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      if (g.probe_wait > 0 && !mbar_wait(smem_u32(&probe_bar), 0u, abort_v, g.probe_wait)) fail();
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+      long long j = 0;
+      for (int it = blockIdx.x; it < tiles && !*abort_v; it += gridDim.x) {
+        const TcItem t = tc_item(g, it);
+        if (t.skip) continue;
+        const int Q = g.nsum * t.nst;
+        for (int q = 0; q < Q && !*abort_v; ++q, ++j) {
+          const int slot = (int)(j % TC_NSTAGE), round = (int)(j / TC_NSTAGE);
+          if (!mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)((round & 1) ^ 1), abort_v)) {
+            if (!*abort_v) fail();
+            break;
           }
+          const int js = q / t.nst, k0 = t.kb + (q % t.nst) * TC_KS;
+          const int bj = t.b * g.nsum + js;
+          const uint32_t dA = smem_u32(smem + slot * TC_STAGE), dB = dA + TC_A_STAGE;
+          const uint32_t fb = smem_u32(&full_bar[slot]);
+          mbar_expect_tx(fb, TC_STAGE);
+          tma_load5(dA, &mapA, 0, t.m0, 0, k0 / 8, bj, fb);
+          tma_load5(dB, &mapB, 0, t.n0, 0, k0 / 8, bj, fb);
         }
+      }
+      // no copy may still be writing shared memory when the CTA exits: the
+      // last TC_NSTAGE stages issued (one per slot) must have landed
+      for (long long jj = j > TC_NSTAGE ? j - TC_NSTAGE : 0; jj < j; ++jj)
+        if (!mbar_wait(smem_u32(&full_bar[jj % TC_NSTAGE]), (uint32_t)((jj / TC_NSTAGE) & 1), nullptr)) fail();
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      long long j = 0;
+      unsigned cycle = 0;
+      const uint32_t a_base = smem_u32(smem);
+      for (int it = blockIdx.x; it < tiles && !*abort_v; it += gridDim.x) {
+        const TcItem t = tc_item(g, it);
+        if (t.skip) continue;
+        const int Q = g.nsum * t.nst;
+        const int nchunks = Q > 0 ? ceil_div_d(Q, TC_DRAIN_STAGES) : 1;
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+          // accumulators drained and zeroed by the epilogue
+          if (!mbar_wait(smem_u32(&acce_bar), cycle & 1u, abort_v)) {
+            if (!*abort_v) fail();
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const int q1 = min(Q, (c + 1) * TC_DRAIN_STAGES);
+          for (int q = c * TC_DRAIN_STAGES; q < q1; ++q, ++j) {
+            const int slot = (int)(j % TC_NSTAGE), round = (int)(j / TC_NSTAGE);
+            if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)(round & 1), abort_v)) {
+              if (!*abort_v) fail();
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = a_base + slot * TC_STAGE, sb = sa + TC_A_STAGE;
+#pragma unroll
+            for (int s1 = 1; s1 <= TC_S; ++s1) {
+              const int ntot = TC_BN * (8 - s1);
+#pragma unroll
+              for (int c0 = 0; c0 < ntot; c0 += 256) {
+                const int nn = min(256, ntot - c0);
+                const uint64_t ad = smem_desc(sa + (s1 - 1) * TC_BM * 16, TC_LBO_A, 128);
+                const uint64_t bd = smem_desc(sb + c0 * 16, TC_LBO_B, 128);
+                mma_bf16(tmem + (uint32_t)(TC_BN * (s1 - 1) + c0), ad, bd, idesc_bf16(TC_BM, nn));
+              }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&empty_bar[slot])));
+          }
+          if (!ok) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&accf_bar)));
+          ++cycle;
+        }
+        if (!ok) break;
+      }
+      // every MMA issued has completed before TMEM is released
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          mbar_addr[buf]));
+          smem_u32(&done_bar)));
+      if (!mbar_wait(smem_u32(&done_bar), 0u, nullptr)) fail();
     }
-    pend[buf] = true;
-    ++chunks_since_drain;
-    ++nchunks;
-    const bool last = q + 1 == Q;
-    if (!last) {  // prefetch stage q + 1 once the MMAs of stage q - 1 released its buffer
-      wait_buf(buf ^ 1);
-      if (ok) load_stage(q + 1, buf ^ 1);
-    }
-    // intermediate drain of the exact groups every 128 k (the final one is
-    // below); every stage writes all six accumulators, so a drain is always
-    // followed by fresh MMAs
-    if (ok && !last && chunks_since_drain * TC_BK >= 128) {
-      wait_buf(buf);  // all MMAs so far complete
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (ok) {
-        // |I| grows by < 2^56.1 per drain: every TC_MAX_DRAINS drains the
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int lq = warp & 3, ch = (warp - 2) >> 2;  // TMEM lane quarter, column quarter
+    const uint32_t tmem_row = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(TC_CPT * ch);
+    const bool aunit = g.alpha == 1.0 || g.alpha == -1.0;
+    const unsigned long long asgn = (aunit && g.alpha < 0.0) ? (1ull << 63) : 0ull;
+    const uint32_t acce = smem_u32(&acce_bar), accf = smem_u32(&accf_bar);
+    // zero every accumulator, then hand them to the MMA issuer
+#pragma unroll
+    for (int a = 0; a < TC_NACC; ++a) tmem_zero16(tmem_row + (uint32_t)(a * TC_BN));
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    mbar_arrive(acce);
+    unsigned cycle = 0;
+    for (int it = blockIdx.x; it < tiles; it += gridDim.x) {
+      const TcItem t = tc_item(g, it);
+      if (t.skip) continue;
+      const int row = t.m0 + 32 * lq + lane;
+      const int cbase = t.n0 + TC_CPT * ch;
+      const int ea = row < g.m ? g.ea[(long long)t.b * g.mpad + row] : 0;
+      const int z = t.b * g.ksplit + t.kpart;
+      double* C = g.C + (long long)z * g.sC;
+      const double* Cin =
+          (g.Cin && t.kpart == 0 && g.beta != 0.0) ? g.Cin + (long long)(t.b / g.bdivC) * g.sCin : nullptr;
+      const int Q = g.nsum * t.nst;
+      const int nchunks = Q > 0 ? ceil_div_d(Q, TC_DRAIN_STAGES) : 1;
+      long long I[TC_CPT];
+#pragma unroll
+      for (int jj = 0; jj < TC_CPT; ++jj) I[jj] = 0;
+      bool flushed = false;
+      int ndrain = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        // uniform over the warp: the TMEM accesses below are warp-collective
+        const bool ok = __all_sync(0xffffffffu, !*abort_v && mbar_wait(accf, cycle & 1u, abort_v));
+        if (!ok) {
+          if (!*abort_v) fail();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const bool last = c + 1 == nchunks;
+        drain_exact(tmem_row, I);
+#pragma unroll
+        for (int a = 0; a < TC_NEXACT; ++a) tmem_zero16(tmem_row + (uint32_t)(a * TC_BN));
+        // |I| grows by < 2^56.1 per drain: every max_drains drains the
         // partial sum is written out before it can leave int64 (K > ~15k)
-        const bool flush = ++ndrain == g.max_drains;
+        const bool flush = !last && ++ndrain == g.max_drains;
+        if (last || flush) {
+          // value = (I + 2^32 (acc7 + acc8)) 2^(ea + eb - 48), then alpha and
+          // beta (acc7 + acc8 only at the end); 8 columns at a time
 #pragma unroll
-        for (int c = 0; c < TC_CPT; c += 16) {
-          long long I[16];
-          ifix_load16(tmem_row, c, I);
-          drain_exact16(tmem_row, c, I);
-          if (flush) {
-            if (row < g.m)
+          for (int h = 0; h < TC_CPT; h += 8) {
+            uint32_t r7[8], r8[8];
+            if (last) {
+              tmem_ld8(tmem_row + (uint32_t)(5 * TC_BN + h), r7);
+              tmem_ld8(tmem_row + (uint32_t)(6 * TC_BN + h), r8);
+            } else {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int col = cbase + c + j;
+              for (int j2 = 0; j2 < 8; ++j2) r7[j2] = r8[j2] = 0u;
+            }
+            if (row < g.m) {
+#pragma unroll
+              for (int j2 = 0; j2 < 8; ++j2) {
+                const int col = cbase + h + j2;
                 if (col < g.n) {
-                  double v = scale_out((double)I[j], ea + g.eb[(long long)b * g.npad + col] - 48, g.alpha, aunit, asgn);
+                  // while |I| < 2^55, I 2^8 plus acc7 rounded at 2^-40 stays
+                  // exact to 2^-57 of the operands' row x column maxima;
+                  // above, acc7 rounded at 2^-32 is below 2^-56 of the result
+                  long long J = I[h + j2];
+                  int e = ea + g.eb[(long long)t.b * g.npad + col] - 48;
+                  const float a7 = __uint_as_float(r7[j2]) + __uint_as_float(r8[j2]);
+                  const bool fine = J > -(1LL << 55) && J < (1LL << 55);
+                  const float tt = a7 * (fine ? 0x1p40f : 0x1p32f);
+                  const long long add =
+                      fabsf(tt) < 2147483648.0f ? (long long)__float2int_rn(tt) : __float2ll_rn(tt);
+                  if (fine) {
+                    J = J * 256 + add;
+                    e -= 8;
+                  } else {
+                    J += add;
+                  }
+                  double v = fix_to_double(J, e);
+                  if (aunit) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)asgn);
+                  else v *= g.alpha;
                   const long long ic = row + (long long)col * g.ldc;
                   if (flushed) v += C[ic];
                   else if (Cin) v = fma(g.beta, Cin[row + (long long)col * g.ldcin], v);
                   C[ic] = v;
                 }
               }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) I[j] = 0;
+            }
           }
-          ifix_store16(tmem_row, c, I);
-        }
-        if (flush) {
-          flushed = true;
-          ndrain = 0;
-        }
-        if (tid == 0) filled &= (1u << (TC_NACC - 1));  // g >= 7 keeps running
-        chunks_since_drain = 0;
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();  // TMEM read before the next MMAs
-    }
-  }
-  // the last stage's MMAs (and any other pending commit)
-  wait_buf(0);
-  wait_buf(1);
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!ok && lane == 0) atomicExch(g.err, 1);
-  // ---- final drain + epilogue, 16 columns at a time (row = this thread's
-  // TMEM lane): value = (I + 2^32 acc_{g>=7}) 2^(ea + eb - 48), then alpha,
-  // beta; about five FP64 operations per output
-  const bool have = ok && nchunks > 0;
-#pragma unroll
-  for (int c0 = 0; c0 < TC_CPT; c0 += 16) {
-    uint32_t r7[16];
-    long long I[16];
-    ifix_load16(tmem_row, c0, I);
-    if (have) {
-      drain_exact16(tmem_row, c0, I);
-      tmem_ld16(tmem_row + (uint32_t)((TC_NACC - 1) * TC_BN + c0), r7);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) r7[j] = 0u;
-    }
-    if (row < g.m) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = cbase + c0 + j;
-        if (col < g.n) {
-          // (I + 2^32 acc7) 2^(ea + eb - 48): while |I| < 2^55, I 2^8 plus
-          // acc7 rounded at 2^-40 stays exact to 2^-57 of the operands'
-          // row x column maxima; above, acc7 rounded at 2^-32 is below 2^-56
-          // of the result
-          long long J = I[j];
-          int e = ea + g.eb[(long long)b * g.npad + col] - 48;
-          const float a7 = __uint_as_float(r7[j]);
-          const bool fine = J > -(1LL << 55) && J < (1LL << 55);
-          const float t = a7 * (fine ? 0x1p40f : 0x1p32f);
-          const long long add = fabsf(t) < 2147483648.0f ? (long long)__float2int_rn(t) : __float2ll_rn(t);
-          if (fine) {
-            J = J * 256 + add;
-            e -= 8;
+          if (last) {
+            tmem_zero16(tmem_row + (uint32_t)(5 * TC_BN));
+            tmem_zero16(tmem_row + (uint32_t)(6 * TC_BN));
           } else {
-            J += add;
+#pragma unroll
+            for (int jj = 0; jj < TC_CPT; ++jj) I[jj] = 0;
+            flushed = true;
+            ndrain = 0;
           }
-          double v = fix_to_double(J, e);
-          if (aunit) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)asgn);
-          else v *= g.alpha;
-          const long long ic = row + (long long)col * g.ldc;
-          if (flushed) v += C[ic];
-          else if (Cin) v = fma(g.beta, Cin[row + (long long)col * g.ldcin], v);
-          C[ic] = ok ? v : NAN;
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        mbar_arrive(acce);
+        ++cycle;
+      }
+      if (*abort_v && row < g.m) {  // unfinished tile: NaN outputs
+#pragma unroll
+        for (int jj = 0; jj < TC_CPT; ++jj)
+          if (cbase + jj < g.n) C[row + (long long)(cbase + jj) * g.ldc] = NAN;
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
 // ---- slicing: exponents of rows of op(A) (cols of op(B)) then the 7 slices
@@ -497,7 +561,9 @@ __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const doubl
   if (q == 0 && ex != INT_MIN && i0 + r < rows) atomicMax(&e[(long long)b * rpad + i0 + r], ex);
 }
 
-// slices q~_s (s = 1..7) of w_j op(X_{b,j}) 2^-e_i, stored [b][j][s][i][kpad]
+// slices q~_s (s = 1..7) of w_j op(X_{b,j}) 2^-e_i, stored as
+// [b][j][k / 8][s][i][k % 8] (rpad rows, kpad / 8 groups of 8 k): the
+// layout the kernel's 5-D TMA boxes read as K-major core matrices
 __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX, long long sXj,
                                 int bdiv, const double* w, const int* e, int rpad, int kpad, __nv_bfloat16* out,
                                 long long sOut, const int* ek, int sgn) {
@@ -508,8 +574,11 @@ __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double*
             ek ? ek + (long long)b * kpad : nullptr, sgn);
   __syncthreads();
   __nv_bfloat16* o = out + ((long long)b * nsum + js) * sOut;
+  const long long sl_stride = (long long)rpad * 8;  // next slice within a k group
   for (int t = threadIdx.x; t < SL_T * SL_T; t += blockDim.x) {
-    const int kk = t % SL_T, ii = t / SL_T;
+    // 8 consecutive k of 4 consecutive rows per warp: 64 contiguous bytes per slice
+    const int k8 = t & 7, ii = (t >> 3) & (SL_T - 1), kg = t >> 9;
+    const int kk = kg * 8 + k8;
     const int i = i0 + ii, k = k0 + kk;
     if (i >= rpad || k >= kpad) continue;
     // X = round(x 2^(56 - e_i)) as a 64-bit integer (|X| <= 2^56), then its
@@ -535,13 +604,56 @@ __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double*
       X = (X - d) >> 8;
     }
     q[0] = (int)X;
+    __nv_bfloat16* dst = o + ((long long)(k >> 3) * TC_S * rpad + i) * 8 + (k & 7);
 #pragma unroll
     for (int sidx = 0; sidx < TC_S; ++sidx)
-      o[(long long)sidx * rpad * kpad + (long long)i * kpad + k] =
-          __float2bfloat16_rn((float)q[sidx] * __int_as_float((127 - 8 * sidx) << 23));
+      dst[sidx * sl_stride] = __float2bfloat16_rn((float)q[sidx] * __int_as_float((127 - 8 * sidx) << 23));
   }
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependence on the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 5-D map over a slice set [nbj][kpad / 8][7][rpad][8] (BF16): box = 8 k x
+// box_rows rows x 7 slices x 2 k groups (one 16-wide stage) x 1 term
+void make_slice_map(CUtensorMap* map, const __nv_bfloat16* base, int rpad, int kpad, int nbj, int box_rows) {
+  auto enc = tensor_map_encoder();
+  if (!enc) throw CudaFail{cudaErrorNotSupported, __FILE__, __LINE__};
+  const cuuint64_t dims[5] = {8, (cuuint64_t)rpad, (cuuint64_t)TC_S, (cuuint64_t)(kpad / 8), (cuuint64_t)nbj};
+  const cuuint64_t strides[4] = {16, (cuuint64_t)16 * rpad, (cuuint64_t)16 * rpad * TC_S,
+                                 (cuuint64_t)16 * rpad * TC_S * (kpad / 8)};
+  const cuuint32_t box[5] = {8, (cuuint32_t)box_rows, (cuuint32_t)TC_S, TC_KS / 8, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw CudaFail{cudaErrorInvalidValue, __FILE__, __LINE__};
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
 
 }  // namespace
 
@@ -629,16 +741,24 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   }
   TcArgs t;
   t.m = g.m; t.n = g.n; t.kpad = kpad; t.nsum = nsum; t.batch = g.batch;
-  t.Asl = Asl; t.Bsl = Bsl; t.ea = ea; t.eb = eb; t.sAsl = sAsl; t.sBsl = sBsl; t.mpad = mpad;
+  t.ea = ea; t.eb = eb; t.mpad = mpad;
   t.npad = same ? mpad : npad;  // row pitch of the B slices and exponents
+  t.tiles_n = npad / TC_BN;
   t.kb_flags = g.kflags; t.ksplit = std::max(1, g.ksplit); t.uplo = g.uplo; t.alpha = re(g.alpha); t.beta = re(g.beta);
   t.Cin = g.Cin; t.ldcin = g.ldcin; t.sCin = g.sCin; t.bdivC = g.bdivC;
   t.C = g.C; t.ldc = g.ldc; t.sC = g.sC; t.err = err;
   t.max_drains = t_tc.flush_every > 0 ? std::min(t_tc.flush_every, TC_MAX_DRAINS) : TC_MAX_DRAINS;
   t.probe_wait = t_tc.probe_wait;
-  ZCSD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-  dim3 grid(mpad / TC_BM, npad / TC_BN, g.batch * t.ksplit);
-  tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(t);
+  CUtensorMap mapA, mapB;
+  make_slice_map(&mapA, Asl, mpad, kpad, g.batch * nsum, TC_BM);
+  make_slice_map(&mapB, Bsl, t.npad, kpad, g.batch * nsum, TC_BN);
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  });
+  const long long items = (long long)(mpad / TC_BM) * (npad / TC_BN) * g.batch * t.ksplit;
+  const int grid = (int)std::min<long long>(items, num_sms());
+  tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(mapA, mapB, t);
   ZCSD_LAUNCH();
   if (tok.slot >= 0) {
     // FP64-equivalent multiply-add work over the tiles executed
