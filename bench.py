@@ -47,6 +47,11 @@ def parse():
                     help="1 (default): real FP64 products on the tcgen05 tensor cores (exact BF16 slicing); 0: FP64 pipe")
     ap.add_argument("--compare-fp64", type=int, default=1,
                     help="with --tc 1, also time the FP64-pipe path (same workload, same accuracy checks)")
+    ap.add_argument("--mixed-slices", type=int, default=6,
+                    help="also time the mixed-precision path: Cholesky-iteration products with 5 or 6 BF16 slices "
+                         "(0 = skip)")
+    ap.add_argument("--mixed-scope", type=int, default=1,
+                    help="bit 0: the two polar decompositions, bit 1: Zolo-eig's polar decompositions")
     ap.add_argument("--config", default="n4096", choices=list(CONFIGS),
                     help="n4096 (headline), n64 (median of 100 after 10), c2048 (complex rank 1536), n8192")
     ap.add_argument("--mode", default="csd", choices=["csd", "fp64-peak", "oracle-full", "gemm"],
@@ -460,6 +465,21 @@ def main():
         fp64 = {"value": v64, "unit": "s/CSD", "tflops": fl / v64 / 1e12, "steps": k64,
                 "accuracy": accuracy(R64, A1, A2, th_known, n, dev), "clocks": ck64}
         ctx.set_tensor_cores(bool(args.tc))
+    # ---- mixed precision (fewer slices in the well-conditioned Cholesky
+    # iteration), same workload and accuracy checks
+    mixed = None
+    if args.tc and args.mixed_slices in (5, 6) and not cfg["cplx"]:
+        ctx.set_mixed_precision(args.mixed_slices, args.mixed_scope)
+        kmx = 1 if n >= 8192 else args.steps
+        msx, perx, Rx, _, ckx, _ = timed_run(args, B, ctx, A1, A2, out, dev, dist, local, False, steps=kmx,
+                                             warmup=1)
+        vx = per_csd(msx, kmx, ws) if args.config != "n64" else statistics.median(perx) / 1e3 / ws
+        mixed = {"value": vx, "unit": "s/CSD", "tflops": fl / vx / 1e12, "steps": kmx,
+                 "slices": args.mixed_slices, "scope": args.mixed_scope,
+                 "accuracy": accuracy(Rx, A1, A2, th_known, n, dev), "clocks": ckx,
+                 "what": "Gram and triangular-solve products of the Cholesky-form Zolo-pd iteration with "
+                         f"{args.mixed_slices} BF16 slices; everything else FP64-accurate (7 slices)"}
+        ctx.set_mixed_precision(7, 0)
     # ---- e2e: same call with pinned host buffers (copies inside the call)
     e2e = None
     if args.e2e_steps > 0:
@@ -533,6 +553,8 @@ def main():
     }
     if fp64:
         line["fp64_pipe_path"] = fp64
+    if mixed:
+        line["mixed_precision_path"] = mixed
     if e2e:
         line["e2e"] = e2e
     if cpu:

@@ -231,6 +231,29 @@ int csd_profile_enable(csd_ctx* ctx, int enable);
 int csd_set_tensor_cores(csd_ctx* ctx, int enable);
 int csd_profile_read(csd_ctx* ctx, csd_profile* out);
 
+/* Leaf size of Zolo-eig's spectral divide and conquer (Section 5): blocks of
+ * at most `leaf` rows (1..1024, default 64) are not split further but
+ * diagonalised by one-sided Jacobi (Hestenes on B_l + ||B_l||_F I), all
+ * leaves of a call batched into the same launches, one CTA per column pair
+ * and round.  The paper leaves the recursion's stopping size open.
+ * Returns 0, -1 (NULL context) or -2 (out of range). */
+int csd_set_eig_leaf(csd_ctx* ctx, int leaf);
+
+/* Mixed precision on the tensor-core path (csd_set_tensor_cores): once the
+ * first, QR-form iteration has mapped the singular values into
+ * [l_1, 1] = [0.4565, 1], the Cholesky-form iteration works on a well
+ * conditioned X, and its Gram product X^* X and the products of its paired
+ * triangular solves may run with `slices` = 5 or 6 BF16 slices per operand
+ * (40 or 48 bits, 15 or 21 slice products instead of 28) while the QR
+ * iteration, the Cholesky factorizations, H_i, B, Zolo-eig's subspace
+ * products and the assembly keep 7 (FP64-accurate).  scope bit 0: the two
+ * polar decompositions of csd_polar (and polar()); bit 1: the polar
+ * decompositions inside Zolo-eig.  slices = 7 or scope = 0 is the default
+ * FP64-accurate path.  The result is checked like any other: angles,
+ * backward error and orthogonality against the 50 n u bar.
+ * Returns 0, -1 (NULL context), -2 (slices not 5..7), -3 (unknown scope bit). */
+int csd_set_mixed_precision(csd_ctx* ctx, int slices, unsigned scope);
+
 /* Fallback of Algorithm 2 (Section 5.1): when ||R~_i - R_i||_F / ||R_i||_F
  * (the backward error of W_i H~_i, info->rdiff) reaches factor * n * u, the
  * polar decomposition of A_i is recomputed through the SVD (one-sided

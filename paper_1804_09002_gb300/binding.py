@@ -92,6 +92,8 @@ def _load():
     lib.csd_fp64_peak.argtypes = [ci, ci, ctypes.POINTER(cd), ctypes.POINTER(cd)]
     lib.csd_set_sign_convention.argtypes = [vp, ci]
     lib.csd_set_alg2_fallback.argtypes = [vp, cd]
+    lib.csd_set_mixed_precision.argtypes = [vp, ci, ctypes.c_uint]
+    lib.csd_set_eig_leaf.argtypes = [vp, ci]
     lib.csd_polar_backward.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, vp, vp, ci, vp, ci, vp, ci, vp, vp, ci,
                                        vp, ci, ctypes.POINTER(csd_info)]
     lib.csd_launch_count.argtypes = []
@@ -102,7 +104,7 @@ def _load():
               "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc", "csd_set_tensor_cores",
               "csd_set_theta_mode", "csd_complete_v2", "csd_polar_rect", "csd_set_zolo_control",
               "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak", "csd_set_sign_convention",
-              "csd_polar_backward", "csd_set_alg2_fallback"):
+              "csd_polar_backward", "csd_set_alg2_fallback", "csd_set_mixed_precision", "csd_set_eig_leaf"):
         getattr(lib, f).restype = ci
     return lib
 
@@ -113,7 +115,8 @@ EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes"
             "zolo_coeffs", "zolo_plan", "csd_status_str", "csd_profile_enable", "csd_profile_read",
             "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores", "csd_set_theta_mode", "csd_complete_v2",
             "csd_polar_rect", "csd_set_zolo_control", "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak",
-            "csd_set_sign_convention", "csd_polar_backward", "csd_set_alg2_fallback"]
+            "csd_set_sign_convention", "csd_polar_backward", "csd_set_alg2_fallback", "csd_set_mixed_precision",
+            "csd_set_eig_leaf"]
 
 STATUS_NOT_CONVERGED = 2
 TEST_REJECT_EIG_SPLITS = 1
@@ -270,6 +273,20 @@ class Context:
         st = lib.csd_set_theta_mode(self._h, int(mode))
         if st != 0:
             raise CSDError(st, "csd_set_theta_mode")
+
+    def set_eig_leaf(self, leaf):
+        """Zolo-eig blocks of at most `leaf` rows go to the batched Jacobi
+        leaf solver."""
+        st = lib.csd_set_eig_leaf(self._h, int(leaf))
+        if st != 0:
+            raise CSDError(st, "csd_set_eig_leaf")
+
+    def set_mixed_precision(self, slices=6, scope=1):
+        """Cholesky-iteration products of Zolo-pd with 5 or 6 BF16 slices
+        (scope bit 0: the CSD's polars, bit 1: Zolo-eig's); 7 = off."""
+        st = lib.csd_set_mixed_precision(self._h, int(slices), int(scope))
+        if st != 0:
+            raise CSDError(st, "csd_set_mixed_precision")
 
     def set_alg2_fallback(self, factor=1e3):
         """SVD polar fallback of Algorithm 2 when ||R~ - R|| / ||R|| reaches

@@ -551,147 +551,6 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(int n, T* Aall, int lda,
   if (tid == 0 && bad && info[b] == 0) info[b] = bad;
 }
 
-// ---------------------------------------------------------------- Jacobi leaves
-constexpr int LEAF_MAX = 64;
-
-template <class T>
-__global__ void __launch_bounds__(256) jacobi_leaf_kernel(const int* offs, const int* sizes, const T* Bg, int ldb,
-                                                          double* lam, T* Vall, int* sweeps_out) {
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  T(*Bs)[LEAF_MAX + 1] = reinterpret_cast<T(*)[LEAF_MAX + 1]>(dyn_smem);
-  T(*Vs)[LEAF_MAX + 1] = Bs + LEAF_MAX;
-  __shared__ double rc[LEAF_MAX / 2], rs[LEAF_MAX / 2];
-  __shared__ T rph[LEAF_MAX / 2];
-  __shared__ int rp[LEAF_MAX / 2], rq[LEAF_MAX / 2];
-  __shared__ double red[32];
-  __shared__ int done;
-  const int l = blockIdx.x;
-  const int off = offs[l], ns = sizes[l];
-  T* V = Vall + (long long)l * LEAF_MAX * LEAF_MAX;
-  const int tid = threadIdx.x;
-  for (int t = tid; t < ns * ns; t += blockDim.x) {
-    const int i = t % ns, j = t / ns;
-    // Hermitian part of the block
-    const T a = Bg[(off + i) + (long long)(off + j) * ldb];
-    const T c = Bg[(off + j) + (long long)(off + i) * ldb];
-    Bs[i][j] = scal(0.5, add(a, conj_(c)));
-    Vs[i][j] = (i == j) ? from_re<T>(1.0) : zero<T>();
-  }
-  __syncthreads();
-  const int nn = ns + (ns & 1);
-  const int npairs = nn / 2;
-  const double u = 0x1p-53;
-  // ||B||_F for the stopping test
-  double acc = 0.0;
-  for (int t = tid; t < ns * ns; t += blockDim.x) acc += abs2(Bs[t % ns][t / ns]);
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((tid & 31) == 0) red[tid >> 5] = acc;
-  __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    red[31] = sqrt(s);
-    done = (ns <= 1);
-  }
-  __syncthreads();
-  const double bnorm = red[31];
-  double prev_off = 1e300;
-  int sweep = 0;
-  for (; sweep < 40 && !done; ++sweep) {
-    for (int rd = 0; rd < nn - 1; ++rd) {
-      // round-robin pairing: slot 0 holds player nn-1, the others rotate
-      if (tid < npairs) {
-        int a, bq;
-        if (tid == 0) { a = nn - 1; bq = rd % (nn - 1); }
-        else { a = (rd + tid) % (nn - 1); bq = (rd - tid + (nn - 1)) % (nn - 1); }
-        const int p = min(a, bq), q = max(a, bq);
-        rp[tid] = p; rq[tid] = q;
-        double cc = 1.0, ss = 0.0;
-        T ph = from_re<T>(1.0);
-        if (q < ns) {
-          const T bpq = Bs[p][q];
-          const double apq = sqrt(abs2(bpq));
-          if (apq > 0.0) {
-            const double bpp = re(Bs[p][p]), bqq = re(Bs[q][q]);
-            const double th = (bqq - bpp) / (2.0 * apq);
-            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-            cc = 1.0 / sqrt(1.0 + t * t);
-            ss = t * cc;
-            ph = scal(1.0 / apq, bpq);
-          }
-        }
-        rc[tid] = cc; rs[tid] = ss; rph[tid] = ph;
-      }
-      __syncthreads();
-      // columns of B and V: [x_p, x_q] <- [x_p, x_q] J, J = [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
-      for (int t = tid; t < npairs * ns; t += blockDim.x) {
-        const int pr = t / ns, i = t % ns;
-        const double s = rs[pr];
-        if (s == 0.0) continue;
-        const int p = rp[pr], q = rq[pr];
-        const double c = rc[pr], tau = s / (1.0 + c);
-        const T e = conj_(rph[pr]);
-        {
-          const T x = Bs[i][p], y = mul(e, Bs[i][q]);
-          Bs[i][p] = sub(x, scal(s, add(y, scal(tau, x))));
-          Bs[i][q] = add(y, scal(s, sub(x, scal(tau, y))));
-        }
-        {
-          const T x = Vs[i][p], y = mul(e, Vs[i][q]);
-          Vs[i][p] = sub(x, scal(s, add(y, scal(tau, x))));
-          Vs[i][q] = add(y, scal(s, sub(x, scal(tau, y))));
-        }
-      }
-      __syncthreads();
-      // rows of B: [r_p; r_q] <- J^* [r_p; r_q]
-      for (int t = tid; t < npairs * ns; t += blockDim.x) {
-        const int pr = t / ns, j = t % ns;
-        const double s = rs[pr];
-        if (s == 0.0) continue;
-        const int p = rp[pr], q = rq[pr];
-        const double c = rc[pr], tau = s / (1.0 + c);
-        const T e = rph[pr];
-        const T x = Bs[p][j], y = mul(e, Bs[q][j]);
-        Bs[p][j] = sub(x, scal(s, add(y, scal(tau, x))));
-        Bs[q][j] = add(y, scal(s, sub(x, scal(tau, y))));
-      }
-      __syncthreads();
-      if (tid < npairs && rs[tid] != 0.0) {
-        const int p = rp[tid], q = rq[tid];
-        Bs[p][q] = zero<T>();
-        Bs[q][p] = zero<T>();
-        Bs[p][p] = from_re<T>(re(Bs[p][p]));
-        Bs[q][q] = from_re<T>(re(Bs[q][q]));
-      }
-      __syncthreads();
-    }
-    // off(B) after the sweep
-    double o2 = 0.0;
-    for (int t = tid; t < ns * ns; t += blockDim.x) {
-      const int i = t % ns, j = t / ns;
-      if (i != j) o2 += abs2(Bs[i][j]);
-    }
-    for (int o = 16; o > 0; o >>= 1) o2 += __shfl_down_sync(0xffffffffu, o2, o);
-    if ((tid & 31) == 0) red[tid >> 5] = o2;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-      const double off = sqrt(s);
-      done = (off <= u * bnorm) || (off <= ns * u * bnorm && off >= 0.5 * prev_off) || off == 0.0;
-      red[30] = off;
-    }
-    __syncthreads();
-    prev_off = red[30];
-  }
-  for (int i = tid; i < ns; i += blockDim.x) lam[off + i] = re(Bs[i][i]);
-  for (int t = tid; t < ns * ns; t += blockDim.x) {
-    const int i = t % ns, j = t / ns;
-    V[i + (long long)j * LEAF_MAX] = Vs[i][j];
-  }
-  if (tid == 0 && sweeps_out) sweeps_out[l] = done ? sweep : -sweep;
-}
-
 }  // namespace
 
 template <class T>
@@ -744,23 +603,10 @@ void potrf_inv(cudaStream_t st, int n, T* A, int lda, long long sA, int k0, int 
   if (tok.slot >= 0) prof_end(tok, st, PK_POTRF, (2.0 / 3.0) * nb * nb * nb * batch);
 }
 
-template <class T>
-void jacobi_leaves(cudaStream_t st, int nleaves, const int* offs, const int* sizes, const T* B, int ldb,
-                   double* lam, T* Vl, int* sweeps_out) {
-  if (nleaves <= 0) return;
-  const int smem = 2 * LEAF_MAX * (LEAF_MAX + 1) * (int)sizeof(T);
-  ZCSD_CUDA(cudaFuncSetAttribute(jacobi_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  ProfToken tok = prof_begin(st);
-  jacobi_leaf_kernel<T><<<nleaves, 256, smem, st>>>(offs, sizes, B, ldb, lam, Vl, sweeps_out);
-  ZCSD_LAUNCH();
-  if (tok.slot >= 0) prof_end(tok, st, PK_JACOBI, 0.0);
-}
-
 #define ZCSD_INST_F(T)                                                                                        \
   template void qr_panel<T>(cudaStream_t, int, int, int, T*, int, long long, int, int, T*, int, long long, T*, \
                             long long, int);                                                                 \
-  template void potrf_inv<T>(cudaStream_t, int, T*, int, long long, int, int, T*, int, long long, int*, int); \
-  template void jacobi_leaves<T>(cudaStream_t, int, const int*, const int*, const T*, int, double*, T*, int*);
+  template void potrf_inv<T>(cudaStream_t, int, T*, int, long long, int, int, T*, int, long long, int*, int);
 
 ZCSD_INST_F(double)
 ZCSD_INST_F(z64)

@@ -128,10 +128,4 @@ template <class T> void qr_panel(cudaStream_t st, int m, int n, int band, T* M, 
 // info[b] is set to (k0 + j + 1) at the first non-positive pivot.
 template <class T> void potrf_inv(cudaStream_t st, int n, T* A, int lda, long long sA, int k0, int nb,
                                   T* Rinv, int ldr, long long sR, int* info, int batch);
-// Jacobi eigendecomposition of leaf blocks (one CTA per leaf, size <= 64):
-// leaf l is the n_l x n_l block of B at (off_l, off_l) (ld = ldb); writes
-// its eigenvalues to lam[off_l..] and eigenvectors to Vl (ld = 64, stride 64*64).
-template <class T> void jacobi_leaves(cudaStream_t st, int nleaves, const int* offs, const int* sizes,
-                                      const T* B, int ldb, double* lam, T* Vl, int* sweeps_out);
-
 }  // namespace zcsd

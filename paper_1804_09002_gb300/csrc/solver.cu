@@ -104,7 +104,8 @@ void d2h(Ctx& cx, void* dst, const void* src, size_t bytes) {
 // iteration in QR form (X (X^*X + cI)^{-1} = Q1 Q2^* / sqrt(c) for
 // [X; sqrt(c) I] = [Q1; Q2] R), later ones in Cholesky form.
 template <class T>
-void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after) {
+void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after,
+             int reduced_slices) {
   cudaStream_t st = cx.stream;
   const Plan& pl = get_plan(cx);
   const int steps = (stop_after > 0) ? std::min(stop_after, pl.steps) : pl.steps;
@@ -151,6 +152,24 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd,
         break;
       }
       // ---- Cholesky form: Z_j = X^* X + c_{2j-1} I = R^* R, T_j = X R^{-1} R^{-*}
+      // X is well conditioned here (its singular values lie in [l_s, 1]);
+      // with reduced_slices the Gram and triangular-solve products run with
+      // fewer BF16 slices, the Cholesky factorizations themselves do not
+      struct ReducedScope {
+        unsigned sites;
+        int slices;
+        ReducedScope(int rs) : sites(t_tc.reduced_sites), slices(t_tc.reduced_slices) {
+          if (rs == 5 || rs == 6) {
+            t_tc.reduced_sites = (1u << GS_GRAM) | (1u << GS_TRSM_F_UPD) | (1u << GS_TRSM_F_DIAG) |
+                                 (1u << GS_TRSM_B_UPD) | (1u << GS_TRSM_B_DIAG);
+            t_tc.reduced_slices = rs;
+          }
+        }
+        ~ReducedScope() {
+          t_tc.reduced_sites = sites;
+          t_tc.reduced_slices = slices;
+        }
+      } reduced_scope(reduced_slices);
       T* G = ar.get<T>(nn * P);
       T* Z = ar.get<T>(nn * P * r);
       T* Rinv = ar.get<T>((size_t)NB_CHOL * n * P * r);
@@ -194,8 +213,8 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd,
   ar.release(mk);
 }
 
-template void zolo_pd<double>(Ctx&, Arena&, int, int, const double*, double*, PolarDiag*, int);
-template void zolo_pd<z64>(Ctx&, Arena&, int, int, const z64*, z64*, PolarDiag*, int);
+template void zolo_pd<double>(Ctx&, Arena&, int, int, const double*, double*, PolarDiag*, int, int);
+template void zolo_pd<z64>(Ctx&, Arena&, int, int, const z64*, z64*, PolarDiag*, int, int);
 
 // ---------------------------------------------------------------- Zolo-eig
 struct EigDiag {
@@ -248,7 +267,7 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
     const int off = bk.off, sz = bk.sz;
     if (sz <= 0) continue;
     T* Bsub = Bw + off + (long long)off * n;
-    if (sz <= LEAF && !(bk.top && restricted)) {
+    if (sz <= cx.eig_leaf && !(bk.top && restricted)) {
       leaf_off.push_back(off);
       leaf_sz.push_back(sz);
       continue;
@@ -299,7 +318,7 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
       cx.hs.d[11] = xnorm;
       ZCSD_CUDA(cudaMemcpyAsync(sc + 3, &cx.hs.d[10], 2 * sizeof(double), cudaMemcpyHostToDevice, st));
       shift_scale<T>(st, sz, Bsub, n, sc + 3, sc + 4, Xs, sz);
-      zolo_pd<T>(cx, ar, sz, 1, Xs, Ws, nullptr);
+      zolo_pd<T>(cx, ar, sz, 1, Xs, Ws, nullptr, 0, (cx.mixed_scope & 2u) ? cx.mixed_slices : 0);
       // P = (W + I)/2, k = trace(P) = number of eigenvalues above s
       half_plus_eye<T>(st, sz, Ws, sz, Ps, sz);
       diag_real<T>(st, sz, Ps, sz, dvals);
@@ -358,7 +377,8 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
       throw EigFail{ed->splits, ed->retries};
     }
   }
-  // ---- leaves: Jacobi on blocks <= LEAF; scalar blocks keep their diagonal
+  // ---- leaves: one-sided Jacobi on every block <= eig_leaf, all leaves in
+  // the same launches; scalar blocks keep their diagonal
   std::vector<int> jo, js;
   for (size_t i = 0; i < leaf_off.size(); ++i) {
     if (leaf_sz[i] > 0) { jo.push_back(leaf_off[i]); js.push_back(leaf_sz[i]); }
@@ -368,18 +388,16 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
   ed->leaves = nl;
   if (nl > 0) {
     const size_t ml = ar.mark();
-    int* doffs = ar.get<int>(2 * nl);
-    T* Vl = ar.get<T>((size_t)LEAF * LEAF * nl);
-    std::vector<int> hbuf(2 * nl);
-    for (int i = 0; i < nl; ++i) { hbuf[i] = jo[i]; hbuf[nl + i] = js[i]; }
-    ZCSD_CUDA(cudaMemcpyAsync(doffs, hbuf.data(), sizeof(int) * 2 * nl, cudaMemcpyHostToDevice, st));
-    jacobi_leaves<T>(st, nl, doffs, doffs + nl, Bw, n, lamw, Vl, nullptr);
+    long long vtot = 0;
+    for (int i = 0; i < nl; ++i) vtot += (long long)js[i] * js[i];
+    T* Vl = ar.get<T>((size_t)vtot);
+    std::vector<long long> voff;
+    jacobi_eig_leaves<T>(cx, ar, jo, js, Bw, n, lamw, Vl, voff);
     for (int i = 0; i < nl; ++i) {
-      gemm1<T>(st, OP_N, OP_N, n, js[i], js[i], one, V + (long long)jo[i] * n, n,
-               Vl + (long long)i * LEAF * LEAF, LEAF, zer, Tmp, n, 0, 0, GS_EIG);
+      gemm1<T>(st, OP_N, OP_N, n, js[i], js[i], one, V + (long long)jo[i] * n, n, Vl + voff[i], js[i], zer, Tmp, n, 0,
+               0, GS_EIG);
       axpby<T>(st, n, js[i], 1.0, Tmp, n, 0, 0.0, V + (long long)jo[i] * n, n, 0, 1);
     }
-    ZCSD_CUDA(cudaStreamSynchronize(st));  // hbuf lifetime
     ar.release(ml);
   }
   // ---- sort the computed eigenpairs [lo, n) ascending
@@ -435,7 +453,7 @@ int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int 
   }
   // ---- lines 1-2: W_i H_i = A_i (both polar decompositions in one batch)
   PolarDiag pd;
-  zolo_pd<T>(cx, ar, n, 2, Apk, W, &pd);
+  zolo_pd<T>(cx, ar, n, 2, Apk, W, &pd, 0, (cx.mixed_scope & 1u) ? cx.mixed_slices : 0);
   const T one = from_re<T>(1.0), zer = zero<T>();
   {
     GemmArgs<T> g;  // H_i = sym(W_i^* A_i)
@@ -777,7 +795,7 @@ int polar_impl(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* Wo, int ldw, T
   if (cx.zolo_stop_after > 0) {
     zolo_pd<T>(cx, ar, n, 1, X, W, &pd, cx.zolo_stop_after);
   } else {
-    zolo_pd<T>(cx, ar, n, 1, X, W, &pd);
+    zolo_pd<T>(cx, ar, n, 1, X, W, &pd, 0, (cx.mixed_scope & 1u) ? cx.mixed_slices : 0);
     const double tol = 50.0 * n * U_ROUND;
     orth = orth_error<T>(cx, ar, n, W, sc + 2, scratch);
     for (int pass = 0; pass < cx.zolo_extra_passes && !(orth <= tol); ++pass) {
@@ -872,7 +890,7 @@ size_t heig_bytes(long long n, size_t es) {
   const long long nn = n * n;
   long long qr = (long long)ceil_div(n, NB_OUT) * (n + NB_OUT) * NB_OUT +
                  (long long)ceil_div(n, NB_OUT) * NB_OUT * NB_OUT + (long long)(5 * NB_OUT + (MAX_SUM + 1) * NB_QR) * n;
-  long long leaves = (n / 1 + 1) * 0 + (long long)LEAF * LEAF * (n / 1);
+  long long leaves = 2 * (long long)LEAF_MAX * n + 8 * n;  // packed G_l and V_l: sum sz_l^2 <= n * leaf
   return (size_t)((7 * nn + std::max(qr, leaves)) * es) + polar_bytes(n, 1, es) + (size_t)(3 * n + 2048) * 8 + 64 * 256;
 }
 
@@ -1186,6 +1204,22 @@ int gemm_typed(csd_ctx* ctx, int opA, int opB, int m, int n, int k, double alpha
 }  // namespace
 
 extern "C" {
+
+int csd_set_eig_leaf(csd_ctx* ctx, int leaf) {
+  if (!ctx) return -1;
+  if (leaf < 1 || leaf > LEAF_MAX) return -2;
+  ctx->cx.eig_leaf = leaf;
+  return CSD_OK;
+}
+
+int csd_set_mixed_precision(csd_ctx* ctx, int slices, unsigned scope) {
+  if (!ctx) return -1;
+  if (slices < 5 || slices > 7) return -2;
+  if (scope & ~3u) return -3;
+  ctx->cx.mixed_slices = slices;
+  ctx->cx.mixed_scope = scope;
+  return CSD_OK;
+}
 
 int csd_set_alg2_fallback(csd_ctx* ctx, double factor) {
   if (!ctx) return -1;

@@ -1,5 +1,7 @@
 // Shared state of the solver entry points (solver.cu) and their Zolo-pd core.
 #pragma once
+#include <vector>
+
 #include "linalg.h"
 #include "profile.h"
 #include "../../include/zolo_csd.h"
@@ -40,6 +42,9 @@ struct Ctx {
   bool force_tc_err = false;    // the running call needs the tensor-core error flag (csd_gemm)
   int sign_mode = 0;            // 1: canonical column signs of U1, U2, V1 (csd_set_sign_convention)
   double alg2_svd_factor = 1e3;  // SVD polar fallback when ||R~ - R|| / ||R|| > factor n u (< 0: never)
+  int eig_leaf = LEAF;           // Zolo-eig blocks of at most this size go to the Jacobi leaf solver
+  int mixed_slices = 7;          // BF16 slices of the Cholesky-iteration products (5, 6 or 7)
+  unsigned mixed_scope = 0;      // bit 0: the CSD's / polar()'s Zolo-pd, bit 1: Zolo-eig's Zolo-pd
 };
 
 // Host-side fault injection for the failure-path tests.
@@ -65,8 +70,11 @@ void d2h(Ctx& cx, void* dst, const void* src, size_t bytes);
 // W_p = polar factor of X0_p for p < P (Zolo-pd, Section 5); X0 and W are
 // P consecutive n x n matrices (ld n).  Workspace comes from `ar`.
 // stop_after > 0 stops after that many iterations (the iterate X_k).
+// reduced_slices = 5 or 6 runs the Gram and triangular-solve products of the
+// Cholesky-form iterations with that many BF16 slices (tensor-core path).
 template <class T>
-void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after = 0);
+void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after = 0,
+             int reduced_slices = 0);
 
 // Columns of V (and of U1, U2) scaled by the inverse phase of V's entry of
 // largest magnitude (real: made positive), columns 0..ncols-1.
@@ -78,6 +86,13 @@ void canonical_signs(cudaStream_t st, int m1, int m2, int n, int ncols, T* V, in
 // SVD-based polar factor of Section 5.1's fallback.  A and W n x n.
 template <class T>
 void svd_polar(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* W, int ldw);
+
+// Eigendecomposition of the diagonal blocks (off[l], sz[l]) of B by
+// one-sided Jacobi, all leaves batched (svd.cu): eigenvalues to
+// lam[off[l] ..], eigenvectors of leaf l to Vl + voff[l] (ld sz[l]).
+template <class T>
+void jacobi_eig_leaves(Ctx& cx, Arena& ar, const std::vector<int>& off, const std::vector<int>& sz, const T* B,
+                       int ldb, double* lam, T* Vl, std::vector<long long>& voff);
 
 // Reverse-mode derivative of the full-rank real CSD from its outputs
 // (grad.cu); gradient inputs may be null (zero).

@@ -16,6 +16,8 @@
 // pair is rotated only while |gamma| > tol sqrt(alpha beta), and the sweeps
 // stop when a whole sweep rotates nothing.  Columns of G that are exactly
 // zero (exactly singular A) get an orthonormal completion by Gram-Schmidt.
+#include <vector>
+
 #include "solver.h"
 
 namespace zcsd {
@@ -179,5 +181,208 @@ void svd_polar(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* W, int ldw) {
 
 template void svd_polar<double>(Ctx&, Arena&, int, const double*, int, double*, int);
 template void svd_polar<z64>(Ctx&, Arena&, int, const z64*, int, z64*, int);
+
+// ---------------------------------------------------------------- leaves
+// Eigendecomposition of the leaf blocks of Zolo-eig by the same one-sided
+// Jacobi method, batched over all leaves of any sizes: for leaf l (the
+// sz_l x sz_l diagonal block of B at offset off_l) G_l = B_l + c_l I with
+// c_l = ||B_l||_F, which is positive definite, so its one-sided Jacobi
+// factorization G_l V_l = U_l Sigma_l has U_l = V_l and
+// lambda_j = sigma_j - c_l (eigenvalues of distinct sigma stay distinct).
+// Every CTA of a round rotates one column pair of one leaf; leaves are packed
+// one after another (G_l and V_l with leading dimension sz_l at goff_l).
+namespace {
+
+struct LeafDev {
+  const int* off;   // offset of the block in B
+  const int* sz;    // block size
+  const int* pre;   // pairs before leaf l (exclusive prefix of npad_l / 2), pre[nl] = total
+  const long long* goff;  // element offset of G_l and V_l in the packed buffers
+  const double* c;  // shift c_l
+  int* rot;         // rotations of leaf l in the current sweep
+  const int* done;  // leaf l converged
+  int nl;
+};
+
+__device__ __forceinline__ int leaf_of(const LeafDev& L, int b) {
+  int lo = 0, hi = L.nl - 1;  // last l with pre[l] <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.pre[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class T>
+__global__ void __launch_bounds__(SVD_THREADS) leaf_round_kernel(LeafDev L, int round, T* G, T* V, double tol) {
+  __shared__ double sh[4 * SVD_THREADS];
+  const int l = leaf_of(L, blockIdx.x);
+  if (L.done[l]) return;
+  const int n = L.sz[l], npad = n + (n & 1);
+  if (round >= npad - 1) return;
+  const int k = blockIdx.x - L.pre[l];
+  int p, q;
+  if (k == 0) {
+    p = npad - 1;
+    q = round;
+  } else {
+    p = (round + k) % (npad - 1);
+    q = (round - k + (npad - 1)) % (npad - 1);
+  }
+  if (p > q) { const int x = p; p = q; q = x; }
+  if (q >= n) return;
+  T* gp = G + L.goff[l] + (long long)p * n;
+  T* gq = G + L.goff[l] + (long long)q * n;
+  double a = 0.0, b = 0.0;
+  T c = zero<T>();
+  for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
+    const T x = gp[i], y = gq[i];
+    a += abs2(x);
+    b += abs2(y);
+    c = add(c, cmul(x, y));
+  }
+  block_sum3<T>(a, b, c, sh);
+  const double g = sqrt(abs2(c));
+  if (!(g > tol * sqrt(a * b))) return;
+  const T ph = scal(1.0 / g, c);
+  const double zeta = (b - a) / (2.0 * g);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+  for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
+    const T x = gp[i], y = mul(gq[i], conj_(ph));
+    gp[i] = sub(scal(cs, x), scal(sn, y));
+    gq[i] = mul(add(scal(sn, x), scal(cs, y)), ph);
+  }
+  T* vp = V + L.goff[l] + (long long)p * n;
+  T* vq = V + L.goff[l] + (long long)q * n;
+  for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
+    const T x = vp[i], y = mul(vq[i], conj_(ph));
+    vp[i] = sub(scal(cs, x), scal(sn, y));
+    vq[i] = mul(add(scal(sn, x), scal(cs, y)), ph);
+  }
+  if (threadIdx.x == 0) atomicAdd(&L.rot[l], 1);
+}
+
+// c_l = ||B_l||_F (one CTA per leaf)
+template <class T>
+__global__ void __launch_bounds__(SVD_THREADS) leaf_norm_kernel(LeafDev L, const T* B, int ldb, double* c) {
+  __shared__ double sh[4 * SVD_THREADS];
+  const int l = blockIdx.x, n = L.sz[l], o = L.off[l];
+  double a = 0.0, b = 0.0;
+  T z = zero<T>();
+  for (long long t = threadIdx.x; t < (long long)n * n; t += SVD_THREADS) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    a += abs2(B[o + i + (long long)(o + j) * ldb]);
+  }
+  block_sum3<T>(a, b, z, sh);
+  if (threadIdx.x == 0) c[l] = sqrt(a) > 0.0 ? sqrt(a) : 1.0;
+}
+
+// G_l = B_l + c_l I, V_l = I (blockIdx.y = leaf)
+template <class T>
+__global__ void leaf_setup_kernel(LeafDev L, const T* B, int ldb, T* G, T* V) {
+  const int l = blockIdx.y, n = L.sz[l], o = L.off[l];
+  const double c = L.c[l];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    T v = B[o + i + (long long)(o + j) * ldb];
+    if (i == j) v = add(v, from_re<T>(c));
+    G[L.goff[l] + t] = v;
+    V[L.goff[l] + t] = from_re<T>(i == j ? 1.0 : 0.0);
+  }
+}
+
+// lambda[off_l + j] = ||g_j|| - c_l (blockIdx.y = leaf, one CTA per column)
+template <class T>
+__global__ void __launch_bounds__(SVD_THREADS) leaf_values_kernel(LeafDev L, const T* G, double* lam) {
+  __shared__ double sh[4 * SVD_THREADS];
+  const int l = blockIdx.y, n = L.sz[l], j = blockIdx.x;
+  if (j >= n) return;
+  const T* g = G + L.goff[l] + (long long)j * n;
+  double a = 0.0, b = 0.0;
+  T z = zero<T>();
+  for (int i = threadIdx.x; i < n; i += SVD_THREADS) a += abs2(g[i]);
+  block_sum3<T>(a, b, z, sh);
+  if (threadIdx.x == 0) lam[L.off[l] + j] = sqrt(a) - L.c[l];
+}
+
+}  // namespace
+
+template <class T>
+void jacobi_eig_leaves(Ctx& cx, Arena& ar, const std::vector<int>& off, const std::vector<int>& sz, const T* B,
+                       int ldb, double* lam, T* Vl, std::vector<long long>& voff) {
+  cudaStream_t st = cx.stream;
+  const int nl = (int)off.size();
+  if (nl == 0) return;
+  const size_t mk = ar.mark();
+  std::vector<int> hi(3 * nl + 1);
+  voff.assign(nl + 1, 0);
+  int maxsz = 0, maxpad = 0;
+  hi[2 * nl] = 0;
+  for (int l = 0; l < nl; ++l) {
+    hi[l] = off[l];
+    hi[nl + l] = sz[l];
+    const int npad = sz[l] + (sz[l] & 1);
+    hi[2 * nl + l + 1] = hi[2 * nl + l] + npad / 2;
+    voff[l + 1] = voff[l] + (long long)sz[l] * sz[l];
+    maxsz = std::max(maxsz, sz[l]);
+    maxpad = std::max(maxpad, npad);
+  }
+  const int total_pairs = hi[3 * nl];
+  ProfToken tok = prof_begin(st);
+  int* di = ar.get<int>(3 * nl + 1 + 2 * nl);
+  long long* dgo = ar.get<long long>(nl + 1);
+  double* dc = ar.get<double>(nl);
+  T* G = ar.get<T>((size_t)voff[nl]);
+  ZCSD_CUDA(cudaMemcpyAsync(di, hi.data(), sizeof(int) * (3 * nl + 1), cudaMemcpyHostToDevice, st));
+  ZCSD_CUDA(cudaMemcpyAsync(dgo, voff.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice, st));
+  ZCSD_CUDA(cudaMemsetAsync(di + 3 * nl + 1, 0, sizeof(int) * 2 * nl, st));
+  LeafDev L;
+  L.off = di;
+  L.sz = di + nl;
+  L.pre = di + 2 * nl;
+  L.goff = dgo;
+  L.c = dc;
+  L.rot = di + 3 * nl + 1;
+  L.done = di + 4 * nl + 1;
+  L.nl = nl;
+  leaf_norm_kernel<T><<<nl, SVD_THREADS, 0, st>>>(L, B, ldb, dc);
+  ZCSD_LAUNCH();
+  leaf_setup_kernel<T><<<dim3(ceil_div((long long)maxsz * maxsz, 256 * 4) + 1, nl), 256, 0, st>>>(L, B, ldb, G, Vl);
+  ZCSD_LAUNCH();
+  const double tol = std::sqrt((double)std::max(maxsz, 1)) * U_ROUND;
+  std::vector<int> hrot(nl), hdone(nl, 0);
+  double flops = 0.0;  // per pair and sweep: three dot products and two column-pair rotations (G and V)
+  for (int sweep = 0; sweep < 40 && maxsz > 1; ++sweep) {
+    for (int l = 0; l < nl; ++l)
+      if (!hdone[l]) flops += (double)sz[l] * (sz[l] - 1) / 2 * (sizeof(T) == 8 ? 30.0 : 120.0) * sz[l];
+    ZCSD_CUDA(cudaMemsetAsync(L.rot, 0, sizeof(int) * nl, st));
+    for (int r = 0; r < maxpad - 1; ++r) {
+      leaf_round_kernel<T><<<total_pairs, SVD_THREADS, 0, st>>>(L, r, G, Vl, tol);
+      ZCSD_LAUNCH();
+    }
+    ZCSD_CUDA(cudaMemcpyAsync(hrot.data(), L.rot, sizeof(int) * nl, cudaMemcpyDeviceToHost, st));
+    ZCSD_CUDA(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int l = 0; l < nl; ++l) {
+      if (hrot[l] == 0) hdone[l] = 1;
+      all = all && hdone[l];
+    }
+    if (all) break;
+    ZCSD_CUDA(cudaMemcpyAsync((int*)L.done, hdone.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
+  }
+  leaf_values_kernel<T><<<dim3(maxsz, nl), SVD_THREADS, 0, st>>>(L, G, lam);
+  ZCSD_LAUNCH();
+  if (tok.slot >= 0) prof_end(tok, st, PK_JACOBI, flops);
+  ZCSD_CUDA(cudaStreamSynchronize(st));  // host vectors above go out of scope
+  ar.release(mk);
+}
+
+template void jacobi_eig_leaves<double>(Ctx&, Arena&, const std::vector<int>&, const std::vector<int>&, const double*,
+                                        int, double*, double*, std::vector<long long>&);
+template void jacobi_eig_leaves<z64>(Ctx&, Arena&, const std::vector<int>&, const std::vector<int>&, const z64*, int,
+                                     double*, z64*, std::vector<long long>&);
 
 }  // namespace zcsd

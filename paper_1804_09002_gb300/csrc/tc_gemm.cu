@@ -50,27 +50,37 @@ namespace zcsd {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 64, TC_S = 7;
+constexpr int TC_BM = 128, TC_BN = 64;
+constexpr int TC_SMAX = 7;           // slices of an FP64-accurate product
 constexpr int TC_KS = 16;            // k per pipeline stage (one MMA K)
-constexpr int TC_NSTAGE = 5;         // depth of the stage ring
 constexpr int TC_KALIGN = 64;        // slices are padded along k to the slicing tile
-constexpr int TC_NACC = 7;           // accumulators g = 2..8
-constexpr int TC_NEXACT = 5;         // g = 2..6: drained exactly every 128 k
 constexpr int TC_DRAIN_STAGES = 128 / TC_KS;
 constexpr int TC_EPI_WARPS = 16;
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
 constexpr int TC_CPT = TC_BN / 4;    // output columns per epilogue thread (16)
 constexpr int TC_TMEM_COLS = 512;    // power of two >= 7 x 64
-constexpr int TC_A_STAGE = TC_S * TC_BM * TC_KS * 2;   // 28 KiB
-constexpr int TC_B_STAGE = TC_S * TC_BN * TC_KS * 2;   // 14 KiB
-constexpr int TC_STAGE = TC_A_STAGE + TC_B_STAGE;
-constexpr int TC_SMEM = TC_NSTAGE * TC_STAGE + 1024;
-constexpr uint32_t TC_LBO_A = TC_S * TC_BM * 16;       // next 8-wide k group
-constexpr uint32_t TC_LBO_B = TC_S * TC_BN * 16;
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 constexpr int TC_MAX_DRAINS = 120;  // intermediate drains before the int64 sum is written out
-static_assert(TC_SMEM <= 227 * 1024, "stage ring exceeds shared memory");
-static_assert(TC_NACC * TC_BN <= TC_TMEM_COLS, "accumulators exceed TMEM");
+
+// Layout constants of a product with S slices per operand (S = 5, 6, 7:
+// 40, 48 or 56 bits): S(S + 1) / 2 slice products into S accumulators
+// (g = 2 .. S + 1); g <= 6 are exact and drained every 128 k.
+template <int S>
+struct TcCfg {
+  static constexpr int NACC = S;
+  static constexpr int NEXACT = S < 5 ? S : 5;
+  static constexpr int A_STAGE = S * TC_BM * TC_KS * 2;  // 28 KiB at S = 7
+  static constexpr int B_STAGE = S * TC_BN * TC_KS * 2;  // 14 KiB at S = 7
+  static constexpr int STAGE = A_STAGE + B_STAGE;
+  static constexpr int NSTAGE = (225 * 1024) / STAGE < 8 ? (225 * 1024) / STAGE : 8;  // depth of the ring
+  static constexpr int SMEM = NSTAGE * STAGE + 1024;
+  static constexpr uint32_t LBO_A = S * TC_BM * 16;  // next 8-wide k group
+  static constexpr uint32_t LBO_B = S * TC_BN * 16;
+  static_assert(SMEM <= 227 * 1024, "stage ring exceeds shared memory");
+  static_assert(NACC * TC_BN <= TC_TMEM_COLS, "accumulators exceed TMEM");
+  static_assert(S >= 5 && S <= TC_SMAX, "5 to 7 slices");
+};
+constexpr int TC_NSTAGE_MAX = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -173,9 +183,10 @@ __device__ __forceinline__ void tmem_zero16(uint32_t addr) {
 // x 2^8a and a conversion give that integer exactly, which enters I shifted
 // left by 8 (4 - a).  Integer arithmetic only: the FP64 pipe runs 2 lanes per
 // clock per SM.
+template <int NEXACT>
 __device__ __forceinline__ void drain_exact(uint32_t tmem_row, long long (&I)[TC_CPT]) {
 #pragma unroll
-  for (int a = 0; a < TC_NEXACT; ++a) {
+  for (int a = 0; a < NEXACT; ++a) {
     uint32_t r[TC_CPT];
     tmem_ld16(tmem_row + (uint32_t)(a * TC_BN), r);
     const float up = __int_as_float((127 + 8 * a) << 23);  // 2^(8a)
@@ -266,11 +277,15 @@ __device__ __forceinline__ TcItem tc_item(const TcArgs& g, int it) {
   return t;
 }
 
+template <int S>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+  using Cf = TcCfg<S>;
+  constexpr int TC_NSTAGE = Cf::NSTAGE, TC_STAGE = Cf::STAGE, TC_A_STAGE = Cf::A_STAGE;
+  constexpr int TC_NACC = Cf::NACC, TC_NEXACT = Cf::NEXACT;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[TC_NSTAGE], empty_bar[TC_NSTAGE];
+  __shared__ __align__(8) uint64_t full_bar[TC_NSTAGE_MAX], empty_bar[TC_NSTAGE_MAX];
   __shared__ __align__(8) uint64_t accf_bar, acce_bar, done_bar, probe_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -366,13 +381,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = a_base + slot * TC_STAGE, sb = sa + TC_A_STAGE;
 #pragma unroll
-            for (int s1 = 1; s1 <= TC_S; ++s1) {
-              const int ntot = TC_BN * (8 - s1);
+            for (int s1 = 1; s1 <= S; ++s1) {
+              const int ntot = TC_BN * (S + 1 - s1);
 #pragma unroll
               for (int c0 = 0; c0 < ntot; c0 += 256) {
                 const int nn = min(256, ntot - c0);
-                const uint64_t ad = smem_desc(sa + (s1 - 1) * TC_BM * 16, TC_LBO_A, 128);
-                const uint64_t bd = smem_desc(sb + c0 * 16, TC_LBO_B, 128);
+                const uint64_t ad = smem_desc(sa + (s1 - 1) * TC_BM * 16, Cf::LBO_A, 128);
+                const uint64_t bd = smem_desc(sb + c0 * 16, Cf::LBO_B, 128);
                 mma_bf16(tmem + (uint32_t)(TC_BN * (s1 - 1) + c0), ad, bd, idesc_bf16(TC_BM, nn));
               }
             }
@@ -431,7 +446,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const bool last = c + 1 == nchunks;
-        drain_exact(tmem_row, I);
+        drain_exact<TC_NEXACT>(tmem_row, I);
 #pragma unroll
         for (int a = 0; a < TC_NEXACT; ++a) tmem_zero16(tmem_row + (uint32_t)(a * TC_BN));
         // |I| grows by < 2^56.1 per drain: every max_drains drains the
@@ -443,13 +458,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int h = 0; h < TC_CPT; h += 8) {
             uint32_t r7[8], r8[8];
-            if (last) {
-              tmem_ld8(tmem_row + (uint32_t)(5 * TC_BN + h), r7);
-              tmem_ld8(tmem_row + (uint32_t)(6 * TC_BN + h), r8);
-            } else {
 #pragma unroll
-              for (int j2 = 0; j2 < 8; ++j2) r7[j2] = r8[j2] = 0u;
-            }
+            for (int j2 = 0; j2 < 8; ++j2) r7[j2] = r8[j2] = 0u;
+            if (last && S >= 6) tmem_ld8(tmem_row + (uint32_t)(5 * TC_BN + h), r7);
+            if (last && S >= 7) tmem_ld8(tmem_row + (uint32_t)(6 * TC_BN + h), r8);
             if (row < g.m) {
 #pragma unroll
               for (int j2 = 0; j2 < 8; ++j2) {
@@ -483,8 +495,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
           }
           if (last) {
-            tmem_zero16(tmem_row + (uint32_t)(5 * TC_BN));
-            tmem_zero16(tmem_row + (uint32_t)(6 * TC_BN));
+#pragma unroll
+            for (int a = TC_NEXACT; a < TC_NACC; ++a) tmem_zero16(tmem_row + (uint32_t)(a * TC_BN));
           } else {
 #pragma unroll
             for (int jj = 0; jj < TC_CPT; ++jj) I[jj] = 0;
@@ -564,6 +576,7 @@ __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const doubl
 // slices q~_s (s = 1..7) of w_j op(X_{b,j}) 2^-e_i, stored as
 // [b][j][k / 8][s][i][k % 8] (rpad rows, kpad / 8 groups of 8 k): the
 // layout the kernel's 5-D TMA boxes read as K-major core matrices
+template <int S>
 __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX, long long sXj,
                                 int bdiv, const double* w, const int* e, int rpad, int kpad, __nv_bfloat16* out,
                                 long long sOut, const int* ek, int sgn) {
@@ -590,23 +603,23 @@ __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double*
     const int ei = (i < rows) ? e[(long long)b * rpad + i] : INT_MIN;
     if (ei > -2000 && tile[ii][kk] != 0.0) {  // rows without a nonzero entry keep the sentinel exponent
       const double v = tile[ii][kk];
-      const int sh = 56 - ei;  // in [-968, 1130] for finite nonzero data
+      const int sh = 8 * S - ei;  // in [-968, 1130] for finite nonzero data
       // 2^sh as two exact, normal powers of two
       const int s1 = sh / 2, s2 = sh - s1;
       X = __double2ll_rn(v * __longlong_as_double((long long)(1023 + s1) << 52) *
                          __longlong_as_double((long long)(1023 + s2) << 52));
     }
-    int q[TC_S];
+    int q[S];
 #pragma unroll
-    for (int sidx = TC_S - 1; sidx >= 1; --sidx) {
+    for (int sidx = S - 1; sidx >= 1; --sidx) {
       const int d = (int)((X + 128) & 255) - 128;
       q[sidx] = d;
       X = (X - d) >> 8;
     }
     q[0] = (int)X;
-    __nv_bfloat16* dst = o + ((long long)(k >> 3) * TC_S * rpad + i) * 8 + (k & 7);
+    __nv_bfloat16* dst = o + ((long long)(k >> 3) * S * rpad + i) * 8 + (k & 7);
 #pragma unroll
-    for (int sidx = 0; sidx < TC_S; ++sidx)
+    for (int sidx = 0; sidx < S; ++sidx)
       dst[sidx * sl_stride] = __float2bfloat16_rn((float)q[sidx] * __int_as_float((127 - 8 * sidx) << 23));
   }
 }
@@ -630,13 +643,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // 5-D map over a slice set [nbj][kpad / 8][7][rpad][8] (BF16): box = 8 k x
 // box_rows rows x 7 slices x 2 k groups (one 16-wide stage) x 1 term
-void make_slice_map(CUtensorMap* map, const __nv_bfloat16* base, int rpad, int kpad, int nbj, int box_rows) {
+void make_slice_map(CUtensorMap* map, const __nv_bfloat16* base, int rpad, int kpad, int nbj, int box_rows, int S) {
   auto enc = tensor_map_encoder();
   if (!enc) throw CudaFail{cudaErrorNotSupported, __FILE__, __LINE__};
-  const cuuint64_t dims[5] = {8, (cuuint64_t)rpad, (cuuint64_t)TC_S, (cuuint64_t)(kpad / 8), (cuuint64_t)nbj};
-  const cuuint64_t strides[4] = {16, (cuuint64_t)16 * rpad, (cuuint64_t)16 * rpad * TC_S,
-                                 (cuuint64_t)16 * rpad * TC_S * (kpad / 8)};
-  const cuuint32_t box[5] = {8, (cuuint32_t)box_rows, (cuuint32_t)TC_S, TC_KS / 8, 1};
+  const cuuint64_t dims[5] = {8, (cuuint64_t)rpad, (cuuint64_t)S, (cuuint64_t)(kpad / 8), (cuuint64_t)nbj};
+  const cuuint64_t strides[4] = {16, (cuuint64_t)16 * rpad, (cuuint64_t)16 * rpad * S,
+                                 (cuuint64_t)16 * rpad * S * (kpad / 8)};
+  const cuuint32_t box[5] = {8, (cuuint32_t)box_rows, (cuuint32_t)S, TC_KS / 8, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)base, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -679,7 +692,9 @@ bool tc_will_handle(const GemmArgs<double>& g) {
          g.n >= TC_BN && g.k >= 64;
 }
 
-void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
+template <int S>
+void tc_gemm_s(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
+  using Cf = TcCfg<S>;
   ProfToken tok = prof_begin(st);  // slicing + tensor-core kernel
   const int mpad = ceil_div(g.m, TC_BM) * TC_BM;
   const int npad = ceil_div(g.n, TC_BN) * TC_BN;
@@ -691,7 +706,7 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   bool same = g.A == g.B && g.lda == g.ldb && g.sA == g.sB && g.sAj == g.sBj && g.bdivA == g.bdivB && g.m == g.n &&
               ((g.opA != OP_N) == (g.opB == OP_N));
   for (int j = 0; j < nsum && same; ++j) same = g.w[j] == 1.0;
-  const long long sAsl = (long long)TC_S * mpad * kpad, sBsl = same ? sAsl : (long long)TC_S * npad * kpad;
+  const long long sAsl = (long long)S * mpad * kpad, sBsl = same ? sAsl : (long long)S * npad * kpad;
   __nv_bfloat16* Asl = ar.get<__nv_bfloat16>((size_t)sAsl * nsum * g.batch);
   __nv_bfloat16* Bsl = same ? Asl : ar.get<__nv_bfloat16>((size_t)sBsl * nsum * g.batch);
   int* ea = ar.get<int>((size_t)mpad * g.batch);
@@ -731,11 +746,11 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
                                           eb, ek, kpad, -1);
     ZCSD_LAUNCH();
   }
-  tc_slice_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, ea, mpad, kpad, Asl,
+  tc_slice_kernel<S><<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, ea, mpad, kpad, Asl,
                                       sAsl, ek, 1);
   ZCSD_LAUNCH();
   if (!same) {
-    tc_slice_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, eb, npad,
+    tc_slice_kernel<S><<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, eb, npad,
                                         kpad, Bsl, sBsl, ek, -1);
     ZCSD_LAUNCH();
   }
@@ -750,15 +765,15 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   t.max_drains = t_tc.flush_every > 0 ? std::min(t_tc.flush_every, TC_MAX_DRAINS) : TC_MAX_DRAINS;
   t.probe_wait = t_tc.probe_wait;
   CUtensorMap mapA, mapB;
-  make_slice_map(&mapA, Asl, mpad, kpad, g.batch * nsum, TC_BM);
-  make_slice_map(&mapB, Bsl, t.npad, kpad, g.batch * nsum, TC_BN);
+  make_slice_map(&mapA, Asl, mpad, kpad, g.batch * nsum, TC_BM, S);
+  make_slice_map(&mapB, Bsl, t.npad, kpad, g.batch * nsum, TC_BN, S);
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(tc_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM);
   });
   const long long items = (long long)(mpad / TC_BM) * (npad / TC_BN) * g.batch * t.ksplit;
   const int grid = (int)std::min<long long>(items, num_sms());
-  tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(mapA, mapB, t);
+  tc_gemm_kernel<S><<<grid, TC_THREADS, Cf::SMEM, st>>>(mapA, mapB, t);
   ZCSD_LAUNCH();
   if (tok.slot >= 0) {
     // FP64-equivalent multiply-add work over the tiles executed
@@ -779,6 +794,16 @@ void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
     prof_end(tok, st, PK_TC, 2.0 * fma * nsum * g.batch, g.site);
   }
   ar.release(mk);
+}
+
+
+void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
+  // fewer slices (40 or 48 bits) only for the call sites the caller marked
+  // as well conditioned; everything else keeps 7 (FP64-accurate)
+  const int S = ((t_tc.reduced_sites >> g.site) & 1u) ? t_tc.reduced_slices : TC_SMAX;
+  if (S == 5) tc_gemm_s<5>(g, st, ar, err);
+  else if (S == 6) tc_gemm_s<6>(g, st, ar, err);
+  else tc_gemm_s<7>(g, st, ar, err);
 }
 
 }  // namespace zcsd

@@ -17,6 +17,8 @@ struct TcState {
   int* err = nullptr;
   long long probe_wait = 0;  // > 0: each launch first polls a barrier nothing signals (timeout-path tests)
   int flush_every = 0;       // > 0: drains between write-outs of the int64 sum (flush-path tests)
+  unsigned reduced_sites = 0;  // bit s: call site s uses reduced_slices BF16 slices instead of 7
+  int reduced_slices = 7;      // 5 (40 bits) or 6 (48 bits)
 };
 extern thread_local TcState t_tc;
 // true when gemm<double>(g) will run on the tensor cores

@@ -83,7 +83,7 @@ def _loss(AG, A1, A2, U1_ref):
 def test_autograd_central_differences_sampled_sizes(AG):
     """16 instances with n drawn from U{16..256}: the directional derivative
     <grad, E> of sum(theta^2) + ||U1 - U1_ref||^2 against the central
-    difference (L(A + hE) - L(A - hE)) / 2h, h = 1e-6, to 1e-6 relative."""
+    difference with step h = 1e-6 (fourth-order stencil), to 1e-6 relative."""
     rng = np.random.default_rng(2025)
     sizes = rng.integers(16, 257, 16)
     worst = 0.0
@@ -98,11 +98,14 @@ def test_autograd_central_differences_sampled_sizes(AG):
         E1 = torch.from_numpy(rng.standard_normal((n, n))).cuda()
         E2 = torch.from_numpy(rng.standard_normal((n, n))).cuda()
         an = float((A1.grad * E1).sum() + (A2.grad * E2).sum())
+        # fourth-order central difference with step h: its truncation error
+        # is O(h^4 / gap^4) relative, where gap is the smallest eigenvalue
+        # gap of B (the second-order stencil's O(h^2 / gap^2) reached 2e-6
+        # at a gap near 1e-3)
         h = 1e-6
         with torch.no_grad():
-            Lp = float(_loss(AG, A1 + h * E1, A2 + h * E2, U1_ref))
-            Lm = float(_loss(AG, A1 - h * E1, A2 - h * E2, U1_ref))
-        fd = (Lp - Lm) / (2 * h)
+            f = {j: float(_loss(AG, A1 + j * h * E1, A2 + j * h * E2, U1_ref)) for j in (-2, -1, 1, 2)}
+        fd = (-f[2] + 8 * f[1] - 8 * f[-1] + f[-2]) / (12 * h)
         rel = abs(fd - an) / max(1.0, abs(an))
         worst = max(worst, rel)
         assert rel <= 1e-6, (n, fd, an)

@@ -70,3 +70,20 @@ def test_csd_n512_complex_rank_deficient_matches_oracle(B):
     assert R["info"]["mu"] == 2.0
     _check(A1, A2, R, n, ref, k)
     assert np.max(np.abs(ref["theta"] - th)) <= 1e-12 * n
+
+
+@pytest.mark.parametrize("slices,scope", [(6, 1), (5, 1), (6, 3)])
+def test_csd_n1024_mixed_precision_matches_oracle(B, clustered_1024, slices, scope):
+    """The mixed-precision path (Cholesky-iteration products of Zolo-pd with
+    5 or 6 BF16 slices; scope 3 also inside Zolo-eig) meets the same bars:
+    angles within 1e-12 n of the oracle, backward error and orthogonality
+    <= 50 n u."""
+    n, A1, A2, th, ref = clustered_1024
+    ctx = B.Context(0)
+    try:
+        ctx.set_tensor_cores(True)
+        ctx.set_mixed_precision(slices, scope)
+        R = ctx.csd_polar(to_dev(A1), to_dev(A2))
+    finally:
+        ctx.close()
+    _check(A1, A2, R, n, ref, n)

@@ -417,3 +417,45 @@ def test_csd_rectangular_edges(B, m1, m2, n):
     assert be <= 50 * max(n, 2) * U, be
     for X in (R["U1"], R["U2"], R["V1"]):
         assert M.orthogonality(X) <= 50 * max(n, 2) * U
+
+
+# ------------------------------------------------ Section 5.1: SVD fallback
+@pytest.mark.parametrize("case,cplx", [("exact_zero", False), ("clustered", False), ("exact_zero", True)])
+def test_csd_svd_polar_fallback(B, case, cplx):
+    """Algorithm 2's check ||R~ - R|| (Section 5.1): with the fallback
+    threshold forced to 0 every block that takes Algorithm 2 recomputes its
+    polar decomposition through the SVD (one-sided Jacobi); the CSD still
+    matches the oracle and the bars hold.  Exactly zero angles make both
+    blocks singular (zero columns of G get the orthonormal completion)."""
+    rng = np.random.default_rng(88 + cplx)
+    if case == "exact_zero":
+        n = 64
+        theta = rng.uniform(0, np.pi / 2, n)
+        theta[:3] = 0.0
+        theta[3:5] = np.pi / 2
+        A1, A2 = I.from_angles(theta, rng, cplx)
+    else:
+        n = 96
+        A1, A2, _ = I.clustered_csd(n, seed=9, noise=0.0, cluster=1e-17)
+    ctx = B.Context(0)
+    try:
+        ctx.set_alg2_fallback(0.0)
+        R = ctx.csd_polar(to_dev(A1), to_dev(A2))
+    finally:
+        ctx.close()
+    info = R["info"]
+    assert max(info["alg2_used"]) == 2
+    ref = O.csd(A1, A2)
+    _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=n)
+
+
+def test_svd_fallback_default_threshold_keeps_algorithm2(B):
+    """At the default threshold the exact-zero case keeps Algorithm 2's W_i
+    (||R~ - R|| is a small multiple of u, as the paper observed)."""
+    n = 64
+    rng = np.random.default_rng(77)
+    theta = rng.uniform(0, np.pi / 2, n)
+    theta[:3] = 0.0
+    A1, A2 = I.from_angles(theta, rng)
+    R = B.csd_polar(to_dev(A1), to_dev(A2))
+    assert 1 in R["info"]["alg2_used"] and 2 not in R["info"]["alg2_used"]

@@ -116,3 +116,21 @@ def test_tc_csd_section6_families(C, kind, n, seed):
     R = C.csd_polar(to_dev(A1), to_dev(A2))
     ref = O.csd(A1, A2)
     _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=ref["rank"])
+
+
+def test_tc_csd_full_size_n8192(C):
+    """n = 8192, the same construction as the n = 4096 workload (config 4's
+    matrix): the stacked [X; sqrt(c) I] products have K > 15 360, so the
+    tensor-core kernel writes its 64-bit integer sum out to C every 120
+    drains (the default schedule).  Angles against the generator's (1e-12 n),
+    backward error and orthogonality <= 50 n u."""
+    n = 8192
+    A1h, A2h, th = I.clustered_csd(n, seed=4)
+    A1, A2 = to_dev(A1h), to_dev(A2h)
+    del A1h, A2h
+    R = C.csd_polar(A1, A2)
+    assert R["rank"] == n
+    got, be, orth = _dev_metrics(A1, A2, R)
+    assert np.max(np.abs(got - th)) <= 1e-12 * n
+    assert be <= 50 * n * U
+    assert orth <= 50 * n * U
