@@ -54,7 +54,8 @@ def parse():
                     help="bit 0: the two polar decompositions, bit 1: Zolo-eig's polar decompositions")
     ap.add_argument("--config", default="n4096", choices=list(CONFIGS),
                     help="n4096 (headline), n64 (median of 100 after 10), c2048 (complex rank 1536), n8192")
-    ap.add_argument("--mode", default="csd", choices=["csd", "fp64-peak", "oracle-full", "gemm"],
+    ap.add_argument("--batch-count", type=int, default=1024, help="--mode batch: number of CSDs")
+    ap.add_argument("--mode", default="csd", choices=["csd", "fp64-peak", "oracle-full", "gemm", "batch"],
                     help="fp64-peak: DFMA / mma.sync f64 microbenchmark; oracle-full: the CPU oracle once at full size")
     return ap.parse_args()
 
@@ -380,6 +381,62 @@ def run_gemm(args):
     print(json.dumps({"mode": "gemm", "n": n, "steps": args.steps, "max_abs_diff_vs_torch": err, **res}), flush=True)
 
 
+def run_batch(args):
+    """Config 5's forward: `--batch-count` real FP64 CSDs with n drawn from
+    U{16..256} (theta uniform, seeds 5000 + i) in one autotuned,
+    graph-captured batch (csd_batch_*); time per batch with CUDA events over
+    K replays (inputs resident in HBM), Sigma 198 n_i^3 flops."""
+    import torch
+    from paper_1804_09002_gb300 import binding as B
+    from paper_1804_09002_gb300 import inputs as I
+    rng = np.random.default_rng(5)
+    sizes = [int(v) for v in rng.integers(16, 257, args.batch_count)]
+    dev = torch.device("cuda", 0)
+    data = [I.haar_csd(n, seed=5000 + i) for i, n in enumerate(sizes)]
+    ctx = B.Context(0)
+    plan = B.Batch(ctx, sizes)
+    plan.load([torch.from_numpy(np.ascontiguousarray(d[0].T)).to(dev).t() for d in data],
+              [torch.from_numpy(np.ascontiguousarray(d[1].T)).to(dev).t() for d in data])
+    t0 = time.perf_counter()
+    plan.run()  # autotune + capture
+    setup_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        plan.run()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev[0].record()
+    for i in range(args.steps):
+        plan.run()
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms = statistics.median(per)
+    fl = sum(198.0 * n ** 3 for n in sizes)
+    worst_be = worst_th = 0.0
+    for i, (n, d) in enumerate(zip(sizes, data)):
+        R = plan.result(i)
+        th = R["theta"]
+        c, s_ = torch.cos(th), torch.sin(th)
+        A1 = torch.from_numpy(d[0]).to(dev)
+        A2 = torch.from_numpy(d[1]).to(dev)
+        num = torch.sqrt(torch.linalg.norm(A1 - (R["U1"] * c) @ R["V1"].T) ** 2 +
+                         torch.linalg.norm(A2 - (R["U2"] * s_) @ R["V1"].T) ** 2)
+        worst_be = max(worst_be, float(num) / np.sqrt(n) / (n * U))
+        worst_th = max(worst_th, float(np.max(np.abs(th.cpu().numpy() - d[2]))) / n)
+    print(json.dumps({"mode": "batch", "metric": "s per batch of CSDs", "value": ms / 1e3, "unit": "s/batch",
+                      "count": len(sizes), "sizes": "n ~ U{16..256}", "csd_per_s": len(sizes) / (ms / 1e3),
+                      "tflops": fl / (ms / 1e3) / 1e12, "flops": fl, "steps": args.steps,
+                      "setup_s_autotune_and_capture": setup_s, "autotuner": plan.stats(),
+                      "status_ok": int(np.sum(plan.status == 0)),
+                      "worst_backward_err_over_nu": worst_be, "worst_theta_err_vs_known_over_n": worst_th,
+                      "clocks": ck}), flush=True)
+    plan.close()
+    ctx.close()
+
+
 def run_oracle_full(args):
     """The CPU oracle once at the full size of --config (no extrapolation)."""
     import platform
@@ -417,6 +474,9 @@ def main():
         return
     if args.mode == "gemm":
         run_gemm(args)
+        return
+    if args.mode == "batch":
+        run_batch(args)
         return
     import torch
     from paper_1804_09002_gb300 import binding as B

@@ -232,8 +232,8 @@ int csd_set_tensor_cores(csd_ctx* ctx, int enable);
 int csd_profile_read(csd_ctx* ctx, csd_profile* out);
 
 /* Leaf size of Zolo-eig's spectral divide and conquer (Section 5): blocks of
- * at most `leaf` rows (1..1024, default 64) are not split further but
- * diagonalised by one-sided Jacobi (Hestenes on B_l + ||B_l||_F I), all
+ * at most `leaf` rows (1..1024, default 256) are not split further but
+ * diagonalised by two-sided cyclic Jacobi (parallel tournament order), all
  * leaves of a call batched into the same launches, one CTA per column pair
  * and round.  The paper leaves the recursion's stopping size open.
  * Returns 0, -1 (NULL context) or -2 (out of range). */
@@ -351,6 +351,43 @@ int csd_gemm(csd_ctx* ctx, int opA, int opB, int m, int n, int k, double alpha, 
  * Allocates and frees a small device buffer.  Returns 0, -k for invalid
  * argument k, or CSD_ERR_CUDA / CSD_ERR_ALLOC. */
 int csd_fp64_peak(int device, int kind, double* tflops, double* ms);
+
+/* Batched CS decompositions: many real FP64 CSDs of different sizes
+ * (n_i <= 1024, full rank) in one CUDA-graph launch.  Independent problems
+ * batched on one GPU, as the paper batches the two polar decompositions and
+ * the r partial-fraction terms of Zolo-pd (Section 3, remark (ii)).
+ * Per instance: Zolo-pd for both blocks (identity-padded to the instance's
+ * size bucket; the padding stays exactly decoupled), B = H2 - H1, its
+ * eigendecomposition by the batched Jacobi leaf solver (one leaf per
+ * instance, at its own size), C, S, theta = atan2(S, C), U_i = W_i V1 and
+ * the ascending order (Algorithm 1).  No Algorithm 2 or 3 branch: an
+ * instance whose angles come out non-finite reports CSD_ERR_INTERNAL in
+ * status[i]; callers with rank-deficient or ill-conditioned blocks use
+ * csd_polar.
+ *
+ * Packed layout (all device pointers): instance i's n_i x n_i matrices are
+ * column-major with leading dimension n_i at element offset
+ * sum_{j<i} n_j^2 of A1, A2, U1, U2 and V1; its angles at sum_{j<i} n_j of
+ * theta.  The plan keeps the sizes; the first csd_batch_run autotunes the
+ * bucket granularity (16, 32 or 64) and, per bucket, the product engine
+ * (FP64-pipe tiles or tensor-core tiles) by timing each on the caller's
+ * data, runs once outside a capture, then captures the whole batch into a
+ * CUDA graph; later runs on the same buffers only launch the graph (new
+ * buffers are captured again).  status (host, count ints, may be NULL)
+ * receives 0 or CSD_ERR_INTERNAL per instance.  The plan owns its device
+ * workspace (grown on demand) and uses the context's stream; destroy the
+ * plan before the context.
+ * create returns 0, -1 (NULL context), -2 (count < 1), -3 (bad sizes),
+ * -4 (NULL plan pointer) or CSD_ERR_ALLOC; run returns 0, -k, or a
+ * CSD_ERR_* code. */
+typedef struct csd_batch csd_batch;
+int csd_batch_create(csd_ctx* ctx, int count, const int* n, csd_batch** plan);
+int csd_batch_run(csd_batch* plan, const double* A1, const double* A2, double* U1, double* U2, double* V1,
+                  double* theta, int* status);
+int csd_batch_destroy(csd_batch* plan);
+/* Autotuner outcome: bucket granularity, number of buckets, buckets on the
+ * tensor cores, and the timed batch (ms) for granularity 16, 32, 64. */
+int csd_batch_stats(const csd_batch* plan, int* granularity, int* buckets, int* tc_buckets, double* tune_ms);
 
 /* Process-wide number of kernels this library has launched so far. */
 long long csd_launch_count(void);

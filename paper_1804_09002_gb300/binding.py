@@ -94,6 +94,10 @@ def _load():
     lib.csd_set_alg2_fallback.argtypes = [vp, cd]
     lib.csd_set_mixed_precision.argtypes = [vp, ci, ctypes.c_uint]
     lib.csd_set_eig_leaf.argtypes = [vp, ci]
+    lib.csd_batch_create.argtypes = [vp, ci, vp, ctypes.POINTER(vp)]
+    lib.csd_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.csd_batch_destroy.argtypes = [vp]
+    lib.csd_batch_stats.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci), vp]
     lib.csd_polar_backward.argtypes = [vp, ci, ci, vp, ci, vp, ci, vp, ci, vp, vp, ci, vp, ci, vp, ci, vp, vp, ci,
                                        vp, ci, ctypes.POINTER(csd_info)]
     lib.csd_launch_count.argtypes = []
@@ -104,7 +108,8 @@ def _load():
               "zolo_plan", "csd_profile_enable", "csd_profile_read", "polar_noalloc", "csd_set_tensor_cores",
               "csd_set_theta_mode", "csd_complete_v2", "csd_polar_rect", "csd_set_zolo_control",
               "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak", "csd_set_sign_convention",
-              "csd_polar_backward", "csd_set_alg2_fallback", "csd_set_mixed_precision", "csd_set_eig_leaf"):
+              "csd_polar_backward", "csd_set_alg2_fallback", "csd_set_mixed_precision", "csd_set_eig_leaf",
+              "csd_batch_create", "csd_batch_run", "csd_batch_destroy", "csd_batch_stats"):
         getattr(lib, f).restype = ci
     return lib
 
@@ -116,7 +121,7 @@ EXPORTED = ["csd_create", "csd_set_stream", "csd_destroy", "csd_workspace_bytes"
             "csd_launch_count", "polar_noalloc", "csd_set_tensor_cores", "csd_set_theta_mode", "csd_complete_v2",
             "csd_polar_rect", "csd_set_zolo_control", "csd_set_test_hooks", "csd_gemm", "csd_fp64_peak",
             "csd_set_sign_convention", "csd_polar_backward", "csd_set_alg2_fallback", "csd_set_mixed_precision",
-            "csd_set_eig_leaf"]
+            "csd_set_eig_leaf", "csd_batch_create", "csd_batch_run", "csd_batch_destroy", "csd_batch_stats"]
 
 STATUS_NOT_CONVERGED = 2
 TEST_REJECT_EIG_SPLITS = 1
@@ -476,6 +481,74 @@ class Context:
         if st != STATUS_OK:
             raise CSDError(st, "heig", info.as_dict())
         return lam, V, info.as_dict()
+
+
+class Batch:
+    """A plan for many real FP64 CSDs of the given sizes (csd_batch_*):
+    the first run autotunes and captures a CUDA graph, later runs on the
+    same packed buffers replay it."""
+
+    def __init__(self, ctx, sizes):
+        import torch
+        self.ctx = ctx
+        self.sizes = [int(v) for v in sizes]
+        self._h = ctypes.c_void_p()
+        n = (ctypes.c_int * len(self.sizes))(*self.sizes)
+        st = lib.csd_batch_create(ctx._h, len(self.sizes), ctypes.cast(n, ctypes.c_void_p), ctypes.byref(self._h))
+        if st != 0:
+            raise CSDError(st, "csd_batch_create")
+        self.off = np.concatenate([[0], np.cumsum([v * v for v in self.sizes])]).astype(np.int64)
+        self.toff = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        dev = torch.device("cuda", ctx.device)
+        tot, ttot = int(self.off[-1]), int(self.toff[-1])
+        self.A1 = torch.empty(tot, dtype=torch.float64, device=dev)
+        self.A2 = torch.empty(tot, dtype=torch.float64, device=dev)
+        self.U1 = torch.empty(tot, dtype=torch.float64, device=dev)
+        self.U2 = torch.empty(tot, dtype=torch.float64, device=dev)
+        self.V1 = torch.empty(tot, dtype=torch.float64, device=dev)
+        self.theta = torch.empty(ttot, dtype=torch.float64, device=dev)
+        self.status = np.zeros(len(self.sizes), dtype=np.int32)
+
+    def _view(self, buf, i):
+        n = self.sizes[i]
+        return buf[int(self.off[i]):int(self.off[i + 1])].view(n, n).t()  # column-major n x n
+
+    def load(self, A1s, A2s):
+        """Copy the inputs (column-major views or any 2-D tensors) into the
+        packed input buffers."""
+        for i, (a1, a2) in enumerate(zip(A1s, A2s)):
+            self._view(self.A1, i).copy_(a1)
+            self._view(self.A2, i).copy_(a2)
+
+    def run(self):
+        self.ctx._bind_stream(self.A1)
+        st = lib.csd_batch_run(self._h, self.A1.data_ptr(), self.A2.data_ptr(), self.U1.data_ptr(),
+                               self.U2.data_ptr(), self.V1.data_ptr(), self.theta.data_ptr(), self.status.ctypes.data)
+        if st != 0:
+            raise CSDError(st, "csd_batch_run")
+        return self.status
+
+    def result(self, i):
+        return dict(U1=self._view(self.U1, i), U2=self._view(self.U2, i), V1=self._view(self.V1, i),
+                    theta=self.theta[int(self.toff[i]):int(self.toff[i + 1])], status=int(self.status[i]))
+
+    def stats(self):
+        g, nb, tcb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        t = (ctypes.c_double * 3)()
+        lib.csd_batch_stats(self._h, ctypes.byref(g), ctypes.byref(nb), ctypes.byref(tcb), ctypes.cast(t, ctypes.c_void_p))
+        return dict(granularity=g.value, buckets=nb.value, tc_buckets=tcb.value,
+                    tune_ms={16: t[0], 32: t[1], 64: t[2]})
+
+    def close(self):
+        if self._h:
+            lib.csd_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _default = {}

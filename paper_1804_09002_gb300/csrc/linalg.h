@@ -11,7 +11,7 @@ namespace zcsd {
 constexpr int NB_QR = 32;    // Householder panel width
 constexpr int NB_OUT = 128;  // outer block of the two-level blocked QR
 constexpr int NB_CHOL = 64;  // Cholesky / TRSM block size
-constexpr int LEAF = 64;     // Zolo-eig leaf size (Jacobi), default
+constexpr int LEAF = 256;    // Zolo-eig leaf size (Jacobi), default
 constexpr int LEAF_MAX = 1024;  // largest leaf size a context may set
 
 struct ArenaOverflow {

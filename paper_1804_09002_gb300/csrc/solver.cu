@@ -105,7 +105,7 @@ void d2h(Ctx& cx, void* dst, const void* src, size_t bytes) {
 // [X; sqrt(c) I] = [Q1; Q2] R), later ones in Cholesky form.
 template <class T>
 void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after,
-             int reduced_slices) {
+             int reduced_slices, bool sync_free) {
   cudaStream_t st = cx.stream;
   const Plan& pl = get_plan(cx);
   const int steps = (stop_after > 0) ? std::min(stop_after, pl.steps) : pl.steps;
@@ -189,9 +189,11 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd,
       for (int j = 0; j < r; ++j) shifts[j] = pl.c[s][2 * j];
       shift_terms<T>(st, n, G, n, nn, shifts, r, Z, n, nn, P);
       cholesky<T>(st, n, Z, n, nn, Rinv, (long long)NB_CHOL * n, info, P * r);
-      d2h(cx, cx.hs.i, info, sizeof(int) * P * r);
       bool ok = true;
-      for (int q = 0; q < P * r; ++q) ok = ok && (cx.hs.i[q] == 0);
+      if (!sync_free) {
+        d2h(cx, cx.hs.i, info, sizeof(int) * P * r);
+        for (int q = 0; q < P * r; ++q) ok = ok && (cx.hs.i[q] == 0);
+      }
       if (!ok) {
         // non-positive pivot: redo this iteration in QR form
         ar.release(mk2);
@@ -213,8 +215,8 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd,
   ar.release(mk);
 }
 
-template void zolo_pd<double>(Ctx&, Arena&, int, int, const double*, double*, PolarDiag*, int, int);
-template void zolo_pd<z64>(Ctx&, Arena&, int, int, const z64*, z64*, PolarDiag*, int, int);
+template void zolo_pd<double>(Ctx&, Arena&, int, int, const double*, double*, PolarDiag*, int, int, bool);
+template void zolo_pd<z64>(Ctx&, Arena&, int, int, const z64*, z64*, PolarDiag*, int, int, bool);
 
 // ---------------------------------------------------------------- Zolo-eig
 struct EigDiag {
@@ -859,6 +861,8 @@ using namespace zcsd;
 struct csd_ctx {
   Ctx cx;
 };
+
+zcsd::Ctx* ctx_internal(csd_ctx* ctx) { return &ctx->cx; }
 
 namespace {
 

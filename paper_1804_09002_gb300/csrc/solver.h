@@ -72,9 +72,12 @@ void d2h(Ctx& cx, void* dst, const void* src, size_t bytes);
 // stop_after > 0 stops after that many iterations (the iterate X_k).
 // reduced_slices = 5 or 6 runs the Gram and triangular-solve products of the
 // Cholesky-form iterations with that many BF16 slices (tensor-core path).
+// sync_free: no device-to-host read (the Cholesky pivot check is skipped:
+// a non-positive pivot leaves NaN, which the caller's checks catch), so the
+// call can be captured in a CUDA graph.
 template <class T>
 void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after = 0,
-             int reduced_slices = 0);
+             int reduced_slices = 0, bool sync_free = false);
 
 // Columns of V (and of U1, U2) scaled by the inverse phase of V's entry of
 // largest magnitude (real: made positive), columns 0..ncols-1.
@@ -86,6 +89,34 @@ void canonical_signs(cudaStream_t st, int m1, int m2, int n, int ncols, T* V, in
 // SVD-based polar factor of Section 5.1's fallback.  A and W n x n.
 template <class T>
 void svd_polar(Ctx& cx, Arena& ar, int n, const T* A, int lda, T* W, int ldw);
+
+// Leaf tables of the batched one-sided Jacobi eigensolver (device arrays in
+// the arena): leaf l is the sz x sz Hermitian block at element offset boff
+// of the B buffer (leading dimension ldb); its eigenvalues go to lam[loff ..]
+// and its G_l, V_l (leading dimension sz) sit at goff in packed buffers of
+// vtot elements.
+struct LeafTable {
+  const long long* boff = nullptr;
+  const int* ldb = nullptr;
+  const int* loff = nullptr;
+  const int* sz = nullptr;
+  const int* pre = nullptr;  // column pairs before leaf l (pre[nl] = total)
+  const long long* goff = nullptr;
+  const long long* roff = nullptr;  // per-row rotation records of leaf l at roff[l]
+  char* rows = nullptr;             // rotation records (rtot of them)
+  double* c = nullptr;       // ||B_l||_F (rotation threshold u ||B_l||_F)
+  int* rot = nullptr;        // rotations of leaf l in the current sweep
+  int* done = nullptr;       // leaf l converged
+  int nl = 0, maxsz = 0, maxpad = 0, total_pairs = 0;
+  long long vtot = 0, rtot = 0;
+  double sweep_flops = 0.0;  // three dot products and two column-pair rotations per pair, all leaves
+};
+LeafTable leaf_table_build(Ctx& cx, Arena& ar, const std::vector<long long>& boff, const std::vector<int>& ldb,
+                           const std::vector<int>& loff, const std::vector<int>& sz);
+// fixed_sweeps > 0: that many sweeps with no device-to-host read (leaves
+// that stop rotating are skipped), for graph capture; 0: until converged.
+template <class T>
+void leaf_solve(Ctx& cx, const LeafTable& L, const T* B, double* lam, T* G, T* V, int fixed_sweeps);
 
 // Eigendecomposition of the diagonal blocks (off[l], sz[l]) of B by
 // one-sided Jacobi, all leaves batched (svd.cu): eigenvalues to

@@ -183,28 +183,27 @@ template void svd_polar<double>(Ctx&, Arena&, int, const double*, int, double*, 
 template void svd_polar<z64>(Ctx&, Arena&, int, const z64*, int, z64*, int);
 
 // ---------------------------------------------------------------- leaves
-// Eigendecomposition of the leaf blocks of Zolo-eig by the same one-sided
-// Jacobi method, batched over all leaves of any sizes: for leaf l (the
-// sz_l x sz_l diagonal block of B at offset off_l) G_l = B_l + c_l I with
-// c_l = ||B_l||_F, which is positive definite, so its one-sided Jacobi
-// factorization G_l V_l = U_l Sigma_l has U_l = V_l and
-// lambda_j = sigma_j - c_l (eigenvalues of distinct sigma stay distinct).
-// Every CTA of a round rotates one column pair of one leaf; leaves are packed
-// one after another (G_l and V_l with leading dimension sz_l at goff_l).
+// Eigendecomposition of the leaf blocks of Zolo-eig by two-sided cyclic
+// Jacobi, batched over all leaves of any sizes.  Leaf l is an sz_l x sz_l
+// Hermitian block B_l (element offset boff_l, leading dimension ldb_l),
+// copied to G_l (leading dimension sz_l, packed at goff_l).  A round of the
+// tournament order rotates n/2 disjoint pairs (p, q); each rotation zeroes
+// g_pq (tan 2 phi = 2 |g_pq| / (g_qq - g_pp), the phase of g_pq moved into
+// column q first) and G <- J^* G J is applied in column-only form, so every
+// access is to a CTA's own two columns:
+//   kernel 1 (one CTA per pair): the angle from g_pp, g_qq, g_pq (entries of
+//     its own columns), the column rotation of G and V, and the rotation
+//     recorded for rows p and q;
+//   kernel 2 (one CTA per pair, the idle column of an odd size included):
+//     the row rotations of every pair applied to the CTA's own columns.
+// Pairs with |g_pq| <= u ||B_l||_F are not rotated; a sweep with no
+// rotation ends the leaf.  The eigenvalues are the diagonal of G.  Unlike
+// one-sided Jacobi on a shifted matrix, every step is a similarity
+// transform of B_l itself, so the eigenvectors carry no shift-dependent
+// error.
 namespace {
 
-struct LeafDev {
-  const int* off;   // offset of the block in B
-  const int* sz;    // block size
-  const int* pre;   // pairs before leaf l (exclusive prefix of npad_l / 2), pre[nl] = total
-  const long long* goff;  // element offset of G_l and V_l in the packed buffers
-  const double* c;  // shift c_l
-  int* rot;         // rotations of leaf l in the current sweep
-  const int* done;  // leaf l converged
-  int nl;
-};
-
-__device__ __forceinline__ int leaf_of(const LeafDev& L, int b) {
+__device__ __forceinline__ int leaf_of(const LeafTable& L, int b) {
   int lo = 0, hi = L.nl - 1;  // last l with pre[l] <= b
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -214,15 +213,18 @@ __device__ __forceinline__ int leaf_of(const LeafDev& L, int b) {
   return lo;
 }
 
-template <class T>
-__global__ void __launch_bounds__(SVD_THREADS) leaf_round_kernel(LeafDev L, int round, T* G, T* V, double tol) {
-  __shared__ double sh[4 * SVD_THREADS];
-  const int l = leaf_of(L, blockIdx.x);
-  if (L.done[l]) return;
-  const int n = L.sz[l], npad = n + (n & 1);
-  if (round >= npad - 1) return;
+// rotation recorded for row i of a leaf in the current round
+struct JRow {
+  int partner;  // the other index of i's pair (-1: i is idle this round)
+  int first;    // i is the smaller index of its pair
+  double c, s, phr, phi;  // rotation and the phase of g_pq (moved into q)
+};
+
+__device__ __forceinline__ void leaf_pair(const LeafTable& L, int round, int& l, int& p, int& q, int& n) {
+  l = leaf_of(L, blockIdx.x);
+  n = L.sz[l];
+  const int npad = n + (n & 1);
   const int k = blockIdx.x - L.pre[l];
-  int p, q;
   if (k == 0) {
     p = npad - 1;
     q = round;
@@ -231,152 +233,234 @@ __global__ void __launch_bounds__(SVD_THREADS) leaf_round_kernel(LeafDev L, int 
     q = (round - k + (npad - 1)) % (npad - 1);
   }
   if (p > q) { const int x = p; p = q; q = x; }
-  if (q >= n) return;
+}
+
+template <class T>
+__device__ __forceinline__ T phase_of(double r, double i);
+template <>
+__device__ __forceinline__ double phase_of<double>(double r, double) { return r; }
+template <>
+__device__ __forceinline__ z64 phase_of<z64>(double r, double i) { return z64{r, i}; }
+
+template <class T>
+__global__ void __launch_bounds__(SVD_THREADS) leaf_col_kernel(LeafTable L, int round, T* G, T* V, JRow* rows) {
+  int l, p, q, n;
+  leaf_pair(L, round, l, p, q, n);
+  if (L.done[l]) return;
+  const int npad = n + (n & 1);
+  if (round >= npad - 1) return;
+  JRow* R = rows + L.roff[l];
+  if (q >= n) {  // p is idle this round
+    if (threadIdx.x == 0 && p < n) R[p] = JRow{-1, 0, 1.0, 0.0, 1.0, 0.0};
+    return;
+  }
   T* gp = G + L.goff[l] + (long long)p * n;
   T* gq = G + L.goff[l] + (long long)q * n;
-  double a = 0.0, b = 0.0;
-  T c = zero<T>();
-  for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
-    const T x = gp[i], y = gq[i];
-    a += abs2(x);
-    b += abs2(y);
-    c = add(c, cmul(x, y));
+  const double gpp = re(gp[p]), gqq = re(gq[q]);
+  const T gpq = gq[p];
+  const double g = sqrt(abs2(gpq));
+  double cs = 1.0, sn = 0.0;
+  T ph = from_re<T>(1.0);
+  const bool rot = g > U_ROUND * L.c[l];
+  if (rot) {
+    ph = scal(1.0 / g, gpq);
+    const double zeta = (gqq - gpp) / (2.0 * g);
+    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    cs = 1.0 / sqrt(1.0 + t * t);
+    sn = cs * t;
+    for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
+      const T x = gp[i], y = mul(gq[i], conj_(ph));
+      gp[i] = sub(scal(cs, x), scal(sn, y));
+      gq[i] = add(scal(sn, x), scal(cs, y));
+    }
+    T* vp = V + L.goff[l] + (long long)p * n;
+    T* vq = V + L.goff[l] + (long long)q * n;
+    for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
+      const T x = vp[i], y = mul(vq[i], conj_(ph));
+      vp[i] = sub(scal(cs, x), scal(sn, y));
+      vq[i] = add(scal(sn, x), scal(cs, y));
+    }
   }
-  block_sum3<T>(a, b, c, sh);
-  const double g = sqrt(abs2(c));
-  if (!(g > tol * sqrt(a * b))) return;
-  const T ph = scal(1.0 / g, c);
-  const double zeta = (b - a) / (2.0 * g);
-  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-  for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
-    const T x = gp[i], y = mul(gq[i], conj_(ph));
-    gp[i] = sub(scal(cs, x), scal(sn, y));
-    gq[i] = mul(add(scal(sn, x), scal(cs, y)), ph);
+  if (threadIdx.x == 0) {
+    R[p] = JRow{q, 1, cs, sn, re(ph), im(ph)};
+    R[q] = JRow{p, 0, cs, sn, re(ph), im(ph)};
+    if (rot) atomicAdd(&L.rot[l], 1);
   }
-  T* vp = V + L.goff[l] + (long long)p * n;
-  T* vq = V + L.goff[l] + (long long)q * n;
-  for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
-    const T x = vp[i], y = mul(vq[i], conj_(ph));
-    vp[i] = sub(scal(cs, x), scal(sn, y));
-    vq[i] = mul(add(scal(sn, x), scal(cs, y)), ph);
+}
+
+template <class T>
+__global__ void __launch_bounds__(SVD_THREADS) leaf_row_kernel(LeafTable L, int round, T* G, const JRow* rows) {
+  int l, p, q, n;
+  leaf_pair(L, round, l, p, q, n);
+  if (L.done[l]) return;
+  const int npad = n + (n & 1);
+  if (round >= npad - 1) return;
+  const JRow* R = rows + L.roff[l];
+  for (int w = 0; w < 2; ++w) {
+    const int col = w == 0 ? p : q;
+    if (col >= n) continue;
+    T* gc = G + L.goff[l] + (long long)col * n;
+    for (int i = threadIdx.x; i < n; i += SVD_THREADS) {
+      const JRow r = R[i];
+      if (!r.first || r.partner < 0) continue;
+      if (r.s == 0.0 && r.phr == 1.0 && r.phi == 0.0) continue;  // not rotated
+      const int j = r.partner;
+      const T ph = phase_of<T>(r.phr, r.phi);
+      const T x = gc[i], y = mul(gc[j], ph);
+      gc[i] = sub(scal(r.c, x), scal(r.s, y));
+      gc[j] = add(scal(r.s, x), scal(r.c, y));
+    }
   }
-  if (threadIdx.x == 0) atomicAdd(&L.rot[l], 1);
 }
 
 // c_l = ||B_l||_F (one CTA per leaf)
 template <class T>
-__global__ void __launch_bounds__(SVD_THREADS) leaf_norm_kernel(LeafDev L, const T* B, int ldb, double* c) {
+__global__ void __launch_bounds__(SVD_THREADS) leaf_norm_kernel(LeafTable L, const T* B) {
   __shared__ double sh[4 * SVD_THREADS];
-  const int l = blockIdx.x, n = L.sz[l], o = L.off[l];
+  const int l = blockIdx.x, n = L.sz[l], ld = L.ldb[l];
+  const T* Bl = B + L.boff[l];
   double a = 0.0, b = 0.0;
   T z = zero<T>();
   for (long long t = threadIdx.x; t < (long long)n * n; t += SVD_THREADS) {
     const int i = (int)(t % n), j = (int)(t / n);
-    a += abs2(B[o + i + (long long)(o + j) * ldb]);
+    a += abs2(Bl[i + (long long)j * ld]);
   }
   block_sum3<T>(a, b, z, sh);
-  if (threadIdx.x == 0) c[l] = sqrt(a) > 0.0 ? sqrt(a) : 1.0;
+  if (threadIdx.x == 0) {
+    L.c[l] = sqrt(a) > 0.0 ? sqrt(a) : 1.0;
+    L.rot[l] = 0;
+    L.done[l] = 0;
+  }
 }
 
-// G_l = B_l + c_l I, V_l = I (blockIdx.y = leaf)
+// G_l = B_l, V_l = I (blockIdx.y = leaf)
 template <class T>
-__global__ void leaf_setup_kernel(LeafDev L, const T* B, int ldb, T* G, T* V) {
-  const int l = blockIdx.y, n = L.sz[l], o = L.off[l];
-  const double c = L.c[l];
+__global__ void leaf_setup_kernel(LeafTable L, const T* B, T* G, T* V) {
+  const int l = blockIdx.y, n = L.sz[l], ld = L.ldb[l];
+  const T* Bl = B + L.boff[l];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * n;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % n), j = (int)(t / n);
-    T v = B[o + i + (long long)(o + j) * ldb];
-    if (i == j) v = add(v, from_re<T>(c));
-    G[L.goff[l] + t] = v;
+    G[L.goff[l] + t] = Bl[i + (long long)j * ld];
     V[L.goff[l] + t] = from_re<T>(i == j ? 1.0 : 0.0);
   }
 }
 
-// lambda[off_l + j] = ||g_j|| - c_l (blockIdx.y = leaf, one CTA per column)
+// after a sweep: a leaf that rotated nothing is done
+__global__ void leaf_sweep_end_kernel(LeafTable L) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L.nl; l += gridDim.x * blockDim.x) {
+    if (L.rot[l] == 0) L.done[l] = 1;
+    L.rot[l] = 0;
+  }
+}
+
+// lambda[loff_l + j] = Re g_jj (blockIdx.y = leaf)
 template <class T>
-__global__ void __launch_bounds__(SVD_THREADS) leaf_values_kernel(LeafDev L, const T* G, double* lam) {
-  __shared__ double sh[4 * SVD_THREADS];
-  const int l = blockIdx.y, n = L.sz[l], j = blockIdx.x;
-  if (j >= n) return;
-  const T* g = G + L.goff[l] + (long long)j * n;
-  double a = 0.0, b = 0.0;
-  T z = zero<T>();
-  for (int i = threadIdx.x; i < n; i += SVD_THREADS) a += abs2(g[i]);
-  block_sum3<T>(a, b, z, sh);
-  if (threadIdx.x == 0) lam[L.off[l] + j] = sqrt(a) - L.c[l];
+__global__ void leaf_values_kernel(LeafTable L, const T* G, double* lam) {
+  const int l = blockIdx.y, n = L.sz[l];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    lam[L.loff[l] + j] = re(G[L.goff[l] + j + (long long)j * n]);
 }
 
 }  // namespace
 
+LeafTable leaf_table_build(Ctx& cx, Arena& ar, const std::vector<long long>& boff, const std::vector<int>& ldb,
+                           const std::vector<int>& loff, const std::vector<int>& sz) {
+  LeafTable L;
+  const int nl = (int)sz.size();
+  L.nl = nl;
+  std::vector<int> hi(5 * nl + 1, 0);
+  std::vector<long long> hl(3 * nl + 2, 0);
+  for (int l = 0; l < nl; ++l) {
+    hi[l] = ldb[l];
+    hi[nl + l] = loff[l];
+    hi[2 * nl + l] = sz[l];
+    const int npad = sz[l] + (sz[l] & 1);
+    hi[3 * nl + l + 1] = hi[3 * nl + l] + npad / 2;
+    hl[l] = boff[l];
+    hl[nl + l + 1] = hl[nl + l] + (long long)sz[l] * sz[l];
+    hl[2 * nl + 1 + l + 1] = hl[2 * nl + 1 + l] + sz[l];
+    L.maxsz = std::max(L.maxsz, sz[l]);
+    L.maxpad = std::max(L.maxpad, npad);
+    L.sweep_flops += (double)sz[l] * (sz[l] - 1) / 2 * 30.0 * sz[l];
+  }
+  L.total_pairs = hi[4 * nl];
+  L.vtot = hl[2 * nl];
+  L.rtot = hl[3 * nl + 1];
+  int* di = ar.get<int>(7 * nl + 1);
+  long long* dl = ar.get<long long>(3 * nl + 2);
+  L.c = ar.get<double>(nl);
+  ZCSD_CUDA(cudaMemcpyAsync(di, hi.data(), sizeof(int) * (4 * nl + 1), cudaMemcpyHostToDevice, cx.stream));
+  ZCSD_CUDA(cudaMemcpyAsync(dl, hl.data(), sizeof(long long) * (3 * nl + 2), cudaMemcpyHostToDevice, cx.stream));
+  ZCSD_CUDA(cudaStreamSynchronize(cx.stream));  // host tables go out of scope
+  L.ldb = di;
+  L.loff = di + nl;
+  L.sz = di + 2 * nl;
+  L.pre = di + 3 * nl;
+  L.rot = di + 4 * nl + 1;
+  L.done = di + 5 * nl + 1;
+  L.boff = dl;
+  L.goff = dl + nl;
+  L.roff = dl + 2 * nl + 1;
+  L.rows = ar.get<char>((size_t)L.rtot * sizeof(JRow));
+  return L;
+}
+
+template <class T>
+void leaf_solve(Ctx& cx, const LeafTable& L, const T* B, double* lam, T* G, T* V, int fixed_sweeps) {
+  cudaStream_t st = cx.stream;
+  if (L.nl == 0) return;
+  ProfToken tok = prof_begin(st);
+  JRow* rows = reinterpret_cast<JRow*>(L.rows);
+  leaf_norm_kernel<T><<<L.nl, SVD_THREADS, 0, st>>>(L, B);
+  ZCSD_LAUNCH();
+  leaf_setup_kernel<T><<<dim3(ceil_div((long long)L.maxsz * L.maxsz, 1024) + 1, L.nl), 256, 0, st>>>(L, B, G, V);
+  ZCSD_LAUNCH();
+  const int nsweeps = fixed_sweeps > 0 ? fixed_sweeps : 40;
+  std::vector<int> hrot(L.nl);
+  double flops = 0.0;
+  for (int sweep = 0; sweep < nsweeps && L.maxsz > 1; ++sweep) {
+    flops += L.sweep_flops * (sizeof(T) == 8 ? 1.0 : 4.0);
+    for (int r = 0; r < L.maxpad - 1; ++r) {
+      leaf_col_kernel<T><<<L.total_pairs, SVD_THREADS, 0, st>>>(L, r, G, V, rows);
+      ZCSD_LAUNCH();
+      leaf_row_kernel<T><<<L.total_pairs, SVD_THREADS, 0, st>>>(L, r, G, rows);
+      ZCSD_LAUNCH();
+    }
+    if (fixed_sweeps <= 0) {  // read the rotation counts: stop once no leaf rotated
+      ZCSD_CUDA(cudaMemcpyAsync(hrot.data(), L.rot, sizeof(int) * L.nl, cudaMemcpyDeviceToHost, st));
+      ZCSD_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int l = 0; l < L.nl; ++l) any = any || hrot[l] != 0;
+      if (!any) break;
+    }
+    leaf_sweep_end_kernel<<<ceil_div(L.nl, 256), 256, 0, st>>>(L);
+    ZCSD_LAUNCH();
+  }
+  leaf_values_kernel<T><<<dim3(ceil_div(L.maxsz, 256), L.nl), 256, 0, st>>>(L, G, lam);
+  ZCSD_LAUNCH();
+  if (tok.slot >= 0) prof_end(tok, st, PK_JACOBI, flops);
+}
+
+template void leaf_solve<double>(Ctx&, const LeafTable&, const double*, double*, double*, double*, int);
+template void leaf_solve<z64>(Ctx&, const LeafTable&, const z64*, double*, z64*, z64*, int);
+
 template <class T>
 void jacobi_eig_leaves(Ctx& cx, Arena& ar, const std::vector<int>& off, const std::vector<int>& sz, const T* B,
                        int ldb, double* lam, T* Vl, std::vector<long long>& voff) {
-  cudaStream_t st = cx.stream;
   const int nl = (int)off.size();
   if (nl == 0) return;
   const size_t mk = ar.mark();
-  std::vector<int> hi(3 * nl + 1);
+  std::vector<long long> boff(nl);
+  std::vector<int> lds(nl, ldb);
   voff.assign(nl + 1, 0);
-  int maxsz = 0, maxpad = 0;
-  hi[2 * nl] = 0;
   for (int l = 0; l < nl; ++l) {
-    hi[l] = off[l];
-    hi[nl + l] = sz[l];
-    const int npad = sz[l] + (sz[l] & 1);
-    hi[2 * nl + l + 1] = hi[2 * nl + l] + npad / 2;
+    boff[l] = off[l] + (long long)off[l] * ldb;
     voff[l + 1] = voff[l] + (long long)sz[l] * sz[l];
-    maxsz = std::max(maxsz, sz[l]);
-    maxpad = std::max(maxpad, npad);
   }
-  const int total_pairs = hi[3 * nl];
-  ProfToken tok = prof_begin(st);
-  int* di = ar.get<int>(3 * nl + 1 + 2 * nl);
-  long long* dgo = ar.get<long long>(nl + 1);
-  double* dc = ar.get<double>(nl);
-  T* G = ar.get<T>((size_t)voff[nl]);
-  ZCSD_CUDA(cudaMemcpyAsync(di, hi.data(), sizeof(int) * (3 * nl + 1), cudaMemcpyHostToDevice, st));
-  ZCSD_CUDA(cudaMemcpyAsync(dgo, voff.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice, st));
-  ZCSD_CUDA(cudaMemsetAsync(di + 3 * nl + 1, 0, sizeof(int) * 2 * nl, st));
-  LeafDev L;
-  L.off = di;
-  L.sz = di + nl;
-  L.pre = di + 2 * nl;
-  L.goff = dgo;
-  L.c = dc;
-  L.rot = di + 3 * nl + 1;
-  L.done = di + 4 * nl + 1;
-  L.nl = nl;
-  leaf_norm_kernel<T><<<nl, SVD_THREADS, 0, st>>>(L, B, ldb, dc);
-  ZCSD_LAUNCH();
-  leaf_setup_kernel<T><<<dim3(ceil_div((long long)maxsz * maxsz, 256 * 4) + 1, nl), 256, 0, st>>>(L, B, ldb, G, Vl);
-  ZCSD_LAUNCH();
-  const double tol = std::sqrt((double)std::max(maxsz, 1)) * U_ROUND;
-  std::vector<int> hrot(nl), hdone(nl, 0);
-  double flops = 0.0;  // per pair and sweep: three dot products and two column-pair rotations (G and V)
-  for (int sweep = 0; sweep < 40 && maxsz > 1; ++sweep) {
-    for (int l = 0; l < nl; ++l)
-      if (!hdone[l]) flops += (double)sz[l] * (sz[l] - 1) / 2 * (sizeof(T) == 8 ? 30.0 : 120.0) * sz[l];
-    ZCSD_CUDA(cudaMemsetAsync(L.rot, 0, sizeof(int) * nl, st));
-    for (int r = 0; r < maxpad - 1; ++r) {
-      leaf_round_kernel<T><<<total_pairs, SVD_THREADS, 0, st>>>(L, r, G, Vl, tol);
-      ZCSD_LAUNCH();
-    }
-    ZCSD_CUDA(cudaMemcpyAsync(hrot.data(), L.rot, sizeof(int) * nl, cudaMemcpyDeviceToHost, st));
-    ZCSD_CUDA(cudaStreamSynchronize(st));
-    bool all = true;
-    for (int l = 0; l < nl; ++l) {
-      if (hrot[l] == 0) hdone[l] = 1;
-      all = all && hdone[l];
-    }
-    if (all) break;
-    ZCSD_CUDA(cudaMemcpyAsync((int*)L.done, hdone.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
-  }
-  leaf_values_kernel<T><<<dim3(maxsz, nl), SVD_THREADS, 0, st>>>(L, G, lam);
-  ZCSD_LAUNCH();
-  if (tok.slot >= 0) prof_end(tok, st, PK_JACOBI, flops);
-  ZCSD_CUDA(cudaStreamSynchronize(st));  // host vectors above go out of scope
+  LeafTable L = leaf_table_build(cx, ar, boff, lds, off, sz);
+  T* G = ar.get<T>((size_t)L.vtot);
+  leaf_solve<T>(cx, L, B, lam, G, Vl, 0);
   ar.release(mk);
 }
 

@@ -219,16 +219,6 @@ __device__ __forceinline__ double fix_to_double(long long J, int e) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
-// d 2^e alpha: the power of two is built from its bits when it is a normal
-// number, with the sign of alpha folded in when |alpha| = 1 (asgn = sign bit)
-__device__ __forceinline__ double scale_out(double d, int e, double alpha, bool unit, unsigned long long asgn) {
-  if (e >= -1022 && e <= 1023) {
-    const double v = d * __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) | asgn));
-    return unit ? v : alpha * v;
-  }
-  return alpha * ldexp(d, e);
-}
-
 struct TcArgs {
   int m, n, kpad, nsum, batch;
   const int* ea;             // [batch][mpad]
@@ -528,6 +518,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // fastest) and the slice writes follow the [i][k] (k fastest) order.
 constexpr int SL_T = 64;
 
+// Per-term weights w_j of a grouped sum, passed by value (no host-to-device
+// copy, so the whole product can be captured in a CUDA graph).
+struct TermWeights {
+  double w[MAX_SUM];
+};
+
 __device__ __forceinline__ void load_tile(double (*tile)[SL_T + 1], const double* X, int ld, int op, int rows, int K,
                                           int i0, int k0, double wj, const int* ek, int sgn) {
   for (int e = threadIdx.x; e < SL_T * SL_T; e += blockDim.x) {
@@ -550,12 +546,12 @@ __device__ __forceinline__ void load_tile(double (*tile)[SL_T + 1], const double
 
 // exponent e_i with max |x| < 2^e_i over row i of w_j op(X_{b,j}), all terms j
 __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX,
-                                  long long sXj, int bdiv, const double* w, int rpad, int* e, const int* ek,
+                                  long long sXj, int bdiv, TermWeights w, int rpad, int* e, const int* ek,
                                   int ekpad, int sgn) {
   __shared__ double tile[SL_T][SL_T + 1];
   const int i0 = blockIdx.x * SL_T, k0 = blockIdx.y * SL_T;
   const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
-  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js],
+  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w.w[js],
             ek ? ek + (long long)b * ekpad : nullptr, sgn);
   __syncthreads();
   // 4 threads per row, then one atomic per row of the tile.  The exponent
@@ -578,12 +574,12 @@ __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const doubl
 // layout the kernel's 5-D TMA boxes read as K-major core matrices
 template <int S>
 __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX, long long sXj,
-                                int bdiv, const double* w, const int* e, int rpad, int kpad, __nv_bfloat16* out,
+                                int bdiv, TermWeights w, const int* e, int rpad, int kpad, __nv_bfloat16* out,
                                 long long sOut, const int* ek, int sgn) {
   __shared__ double tile[SL_T][SL_T + 1];
   const int i0 = blockIdx.x * SL_T, k0 = blockIdx.y * SL_T;
   const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
-  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w[js],
+  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w.w[js],
             ek ? ek + (long long)b * kpad : nullptr, sgn);
   __syncthreads();
   __nv_bfloat16* o = out + ((long long)b * nsum + js) * sOut;
@@ -711,11 +707,9 @@ void tc_gemm_s(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) 
   __nv_bfloat16* Bsl = same ? Asl : ar.get<__nv_bfloat16>((size_t)sBsl * nsum * g.batch);
   int* ea = ar.get<int>((size_t)mpad * g.batch);
   int* eb = same ? ea : ar.get<int>((size_t)npad * g.batch);
-  double* w = ar.get<double>(2 * MAX_SUM);
-  // host weights -> device (term weights apply to A; B gets unit weights)
-  double hw[2 * MAX_SUM];
-  for (int j = 0; j < MAX_SUM; ++j) { hw[j] = g.w[j]; hw[MAX_SUM + j] = 1.0; }
-  ZCSD_CUDA(cudaMemcpyAsync(w, hw, sizeof(hw), cudaMemcpyHostToDevice, st));
+  // term weights apply to A; B gets unit weights
+  TermWeights w, wunit;
+  for (int j = 0; j < MAX_SUM; ++j) { w.w[j] = g.w[j]; wunit.w[j] = 1.0; }
   // 0xC0C0C0C0 = -1061109568: "no nonzero entry"; two of them still add up
   // without overflow, and such rows/columns have all-zero slices
   ZCSD_CUDA(cudaMemsetAsync(ea, 0xC0, sizeof(int) * mpad * g.batch, st));
@@ -735,14 +729,14 @@ void tc_gemm_s(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) 
     ZCSD_CUDA(cudaMemsetAsync(ek, 0xC0, sizeof(int) * kpad * g.batch, st));
     const dim3 gk(kpad / SL_T, ceil_div(g.n, SL_T), g.batch);
     tc_row_exp_kernel<<<gk, 256, 0, st>>>(g.k, g.n, 1, g.opB == OP_N ? OP_N : OP_T, g.B, g.ldb, g.sB, 0, g.bdivB,
-                                          w + MAX_SUM, kpad, ek, nullptr, 0, 0);
+                                          wunit, kpad, ek, nullptr, 0, 0);
     ZCSD_LAUNCH();
   }
   tc_row_exp_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, mpad, ea, ek, kpad,
                                         1);
   ZCSD_LAUNCH();
   if (!same) {
-    tc_row_exp_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, npad,
+    tc_row_exp_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, wunit, npad,
                                           eb, ek, kpad, -1);
     ZCSD_LAUNCH();
   }
@@ -750,7 +744,7 @@ void tc_gemm_s(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) 
                                       sAsl, ek, 1);
   ZCSD_LAUNCH();
   if (!same) {
-    tc_slice_kernel<S><<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, w + MAX_SUM, eb, npad,
+    tc_slice_kernel<S><<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, wunit, eb, npad,
                                         kpad, Bsl, sBsl, ek, -1);
     ZCSD_LAUNCH();
   }
