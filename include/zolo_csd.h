@@ -227,7 +227,10 @@ int csd_profile_enable(csd_ctx* ctx, int enable);
  * factorization (site 3) are of the size of sqrt(c) and need accuracy
  * relative to themselves: that product is also balanced along its inner
  * dimension by powers of two (A D, D^-1 B, D = diag of the row maxima of B).
- * Complex data always uses the FP64 pipe.  Returns 0 or -1 (NULL context). */
+ * Complex products with real alpha and beta run as two real grouped sums
+ * over the interleaved parts (Re C = Re A Re B - Im A Im B,
+ * Im C = Re A Im B + Im A Re B); grouped complex sums and the balanced
+ * product stay on the FP64 pipe.  Returns 0 or -1 (NULL context). */
 int csd_set_tensor_cores(csd_ctx* ctx, int enable);
 int csd_profile_read(csd_ctx* ctx, csd_profile* out);
 

@@ -221,6 +221,9 @@ struct csd_batch {
   double tune_ms[3] = {0, 0, 0};        // autotuner: batch time per granularity (16, 32, 64)
   bool tuned = false;
   double ws_scale = 1.0;                // grows when a run overflows the arena
+  size_t run_need = 0;                  // arena bytes a run was seen to need
+  cudaStream_t stream = nullptr;        // the plan's own stream (tuning, capture, replay)
+  cudaEvent_t ev = nullptr;
 };
 
 namespace {
@@ -277,7 +280,7 @@ int build_buckets(csd_batch* b, int gran) {
     run = std::max(run, bucket_bytes(bk));
   }
   b->persist_bytes = (pbytes + 255) & ~(size_t)255;
-  b->ws_bytes = b->persist_bytes + (size_t)((double)run * b->ws_scale);
+  b->ws_bytes = b->persist_bytes + std::max((size_t)((double)run * b->ws_scale), b->run_need);
   if (cudaMalloc((void**)&b->ws, b->ws_bytes) != cudaSuccess) {
     cudaGetLastError();
     b->ws = nullptr;
@@ -434,6 +437,27 @@ int csd_batch_run(csd_batch* b, const double* A1, const double* A2, double* U1, 
     ProfOff() : prev(t_prof) { t_prof = nullptr; }
     ~ProfOff() { t_prof = prev; }
   } prof_off;
+  // the batch runs on the plan's own non-blocking stream (a capture needs a
+  // stream other than the legacy default one), ordered after the work
+  // already queued on the context's stream and before whatever follows it
+  if (!b->stream) {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return CSD_ERR_CUDA;
+    }
+  }
+  struct StreamSwap {
+    Ctx& c;
+    cudaStream_t prev;
+    StreamSwap(Ctx& c_, cudaStream_t s) : c(c_), prev(c_.stream) { c.stream = s; }
+    ~StreamSwap() { c.stream = prev; }
+  };
+  if (cudaEventRecord(b->ev, cx.stream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return CSD_ERR_CUDA;
+  }
+  StreamSwap swap(cx, b->stream);
   for (int attempt = 0;; ++attempt) {
    try {
     if (!b->tuned) {
@@ -463,7 +487,7 @@ int csd_batch_run(csd_batch* b, const double* A1, const double* A2, double* U1, 
     if (status) ZCSD_CUDA(cudaMemcpy(status, b->dstatus, sizeof(int) * b->count, cudaMemcpyDeviceToHost));
     if (err) return CSD_ERR_DEVICE_TIMEOUT;
     return CSD_OK;
-   } catch (ArenaOverflow&) {
+   } catch (ArenaOverflow& o) {
     // a run needed more workspace than estimated: grow it and redo the set-up
     cudaStreamCaptureStatus cs;
     if (cudaStreamIsCapturing(cx.stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
@@ -473,8 +497,9 @@ int csd_batch_run(csd_batch* b, const double* A1, const double* A2, double* U1, 
     }
     cudaStreamSynchronize(cx.stream);
     cudaGetLastError();
-    if (attempt >= 3) return CSD_ERR_INTERNAL;
+    if (attempt >= 6) return CSD_ERR_INTERNAL;
     b->ws_scale *= 2.0;
+    b->run_need = std::max(b->run_need, o.needed + o.needed / 4);
     std::vector<char> tcs;
     for (auto& bk : b->buckets) tcs.push_back(bk.tc);
     const bool tuned = b->tuned;
@@ -501,8 +526,10 @@ int csd_batch_run(csd_batch* b, const double* A1, const double* A2, double* U1, 
 int csd_batch_destroy(csd_batch* b) {
   if (!b) return CSD_OK;
   cudaSetDevice(b->cx->device);
-  cudaStreamSynchronize(b->cx->stream);
+  if (b->stream) cudaStreamSynchronize(b->stream);
   free_plan_ws(b);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return CSD_OK;
 }

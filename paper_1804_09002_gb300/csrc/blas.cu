@@ -178,6 +178,11 @@ void gemm(const GemmArgs<T>& g, cudaStream_t st) {
       tc_gemm(g, st, *t_tc.ar, t_tc.err);
       return;
     }
+  } else {
+    if (tc_will_handle_complex(g)) {
+      tc_gemm_complex(g, st, *t_tc.ar, t_tc.err);
+      return;
+    }
   }
   const bool narrow = g.m <= 32;
   ProfToken tok = prof_begin(st);

@@ -476,7 +476,15 @@ template <class T, int CL>
 void launch_panel_smem(cudaStream_t st, int m, int n, int band, T* M, int ldm, long long sM, int k0, int nb, T* Y,
                        int ldy, long long sY, T* Tf, long long sT, int batch, int chunk) {
   const int smem = PANEL_MAXNB * chunk * (int)sizeof(T);
-  ZCSD_CUDA(cudaFuncSetAttribute(qr_panel_smem_kernel<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  // the attribute is set once per kernel (to the largest dynamic shared
+  // memory its launches use, PANEL_SMEM_MAX), not per launch: launches may
+  // be graph-captured
+  static const bool attr_set = [] {
+    ZCSD_CUDA(cudaFuncSetAttribute(qr_panel_smem_kernel<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   PANEL_SMEM_MAX));
+    return true;
+  }();
+  (void)attr_set;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(batch * CL, 1, 1);
   cfg.blockDim = dim3(PANEL_CL_THREADS, 1, 1);
@@ -596,7 +604,11 @@ void potrf_inv(cudaStream_t st, int n, T* A, int lda, long long sA, int k0, int 
                long long sR, int* info, int batch) {
   if (nb > CHOL_MAXNB) throw CudaFail{cudaErrorInvalidValue, __FILE__, __LINE__};
   const int smem = 2 * CHOL_MAXNB * (CHOL_MAXNB + 1) * (int)sizeof(T);
-  ZCSD_CUDA(cudaFuncSetAttribute(potrf_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  static const bool attr_set = [smem] {
+    ZCSD_CUDA(cudaFuncSetAttribute(potrf_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return true;
+  }();
+  (void)attr_set;
   ProfToken tok = prof_begin(st);
   potrf_inv_kernel<T><<<batch, 256, smem, st>>>(n, A, lda, sA, k0, nb, Rinv, ldr, sR, info);
   ZCSD_LAUNCH();

@@ -35,10 +35,16 @@ static int pick_ksplit(int m, int n, int k, int batch, int bm, int kmin = 256) {
 template <class T>
 static int resolve_ksplit(GemmArgs<T>& g, int ks, int cap) {
   g.ksplit = std::max(1, std::min(ks, cap));
+  GemmArgs<T> probe = g;
+  probe.ksplit = 1;
   if constexpr (std::is_same<T, double>::value) {
-    GemmArgs<T> probe = g;
-    probe.ksplit = 1;
     if (tc_will_handle(probe)) g.ksplit = tc_pick_ksplit(probe, cap);
+  } else {
+    if (tc_will_handle_complex(probe)) {
+      GemmArgs<double> r;  // the real products it becomes: same tiles
+      r.m = g.m; r.n = g.n; r.k = g.k; r.batch = g.batch;
+      g.ksplit = tc_pick_ksplit(r, cap);
+    }
   }
   return g.ksplit;
 }

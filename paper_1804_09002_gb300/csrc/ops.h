@@ -45,6 +45,8 @@ struct GemmArgs {
   int site = 0;                 // call-site label for kernel accounting (GemmSite)
   int ksplit = 1;               // split-K: problem b, part s writes C_{b*ksplit+s} (Cin/beta only in part 0)
   int kbal = 0;                 // tensor-core path: balance the inner dimension by the row maxima of op(B)
+  int es = 1;                   // tensor-core path: element stride in doubles of A, B, Cin, C (2: one part of
+                                // interleaved complex data; ld and problem strides stay in elements)
   GemmArgs() { for (int i = 0; i < MAX_SUM; ++i) w[i] = 1.0; }
 };
 

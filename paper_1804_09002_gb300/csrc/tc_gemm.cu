@@ -232,6 +232,7 @@ struct TcArgs {
   const double* Cin; int ldcin; long long sCin; int bdivC;
   double* C; int ldc; long long sC;
   int* err;
+  int es;                  // element stride of C and Cin in doubles (2: one part of complex data)
   int max_drains;          // drains between write-outs of the int64 sum
   long long probe_wait;    // > 0: first poll a barrier nothing signals (timeout-path tests)
 };
@@ -417,9 +418,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int cbase = t.n0 + TC_CPT * ch;
       const int ea = row < g.m ? g.ea[(long long)t.b * g.mpad + row] : 0;
       const int z = t.b * g.ksplit + t.kpart;
-      double* C = g.C + (long long)z * g.sC;
+      double* C = g.C + (long long)z * g.sC * g.es;
       const double* Cin =
-          (g.Cin && t.kpart == 0 && g.beta != 0.0) ? g.Cin + (long long)(t.b / g.bdivC) * g.sCin : nullptr;
+          (g.Cin && t.kpart == 0 && g.beta != 0.0) ? g.Cin + (long long)(t.b / g.bdivC) * g.sCin * g.es : nullptr;
       const int Q = g.nsum * t.nst;
       const int nchunks = Q > 0 ? ceil_div_d(Q, TC_DRAIN_STAGES) : 1;
       long long I[TC_CPT];
@@ -476,9 +477,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   double v = fix_to_double(J, e);
                   if (aunit) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)asgn);
                   else v *= g.alpha;
-                  const long long ic = row + (long long)col * g.ldc;
+                  const long long ic = (row + (long long)col * g.ldc) * g.es;
                   if (flushed) v += C[ic];
-                  else if (Cin) v = fma(g.beta, Cin[row + (long long)col * g.ldcin], v);
+                  else if (Cin) v = fma(g.beta, Cin[(row + (long long)col * g.ldcin) * g.es], v);
                   C[ic] = v;
                 }
               }
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (*abort_v && row < g.m) {  // unfinished tile: NaN outputs
 #pragma unroll
         for (int jj = 0; jj < TC_CPT; ++jj)
-          if (cbase + jj < g.n) C[row + (long long)(cbase + jj) * g.ldc] = NAN;
+          if (cbase + jj < g.n) C[(row + (long long)(cbase + jj) * g.ldc) * g.es] = NAN;
       }
     }
   }
@@ -525,7 +526,7 @@ struct TermWeights {
 };
 
 __device__ __forceinline__ void load_tile(double (*tile)[SL_T + 1], const double* X, int ld, int op, int rows, int K,
-                                          int i0, int k0, double wj, const int* ek, int sgn) {
+                                          int i0, int k0, double wj, const int* ek, int sgn, int es) {
   for (int e = threadIdx.x; e < SL_T * SL_T; e += blockDim.x) {
     // a = fastest index in memory, c = the other
     const int a = e % SL_T, c = e / SL_T;
@@ -534,7 +535,7 @@ __device__ __forceinline__ void load_tile(double (*tile)[SL_T + 1], const double
     else { k = k0 + a; i = i0 + c; }
     double v = 0.0;
     if (i < rows && k < K) {
-      v = wj * (op == OP_N ? X[i + (long long)k * ld] : X[k + (long long)i * ld]);
+      v = wj * (op == OP_N ? X[es * (i + (long long)k * ld)] : X[es * (k + (long long)i * ld)]);
       if (ek) {  // inner-dimension balance: x 2^(sgn e_k), exact (sentinel e_k: zero row of op(B), no shift)
         const int sh = ek[k] < -2000 ? 0 : sgn * ek[k];
         v = (sh >= -1022 && sh <= 1023) ? v * __longlong_as_double((long long)(sh + 1023) << 52) : ldexp(v, sh);
@@ -547,12 +548,12 @@ __device__ __forceinline__ void load_tile(double (*tile)[SL_T + 1], const double
 // exponent e_i with max |x| < 2^e_i over row i of w_j op(X_{b,j}), all terms j
 __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX,
                                   long long sXj, int bdiv, TermWeights w, int rpad, int* e, const int* ek,
-                                  int ekpad, int sgn) {
+                                  int ekpad, int sgn, int es) {
   __shared__ double tile[SL_T][SL_T + 1];
   const int i0 = blockIdx.x * SL_T, k0 = blockIdx.y * SL_T;
   const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
-  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w.w[js],
-            ek ? ek + (long long)b * ekpad : nullptr, sgn);
+  load_tile(tile, X + (long long)(b / bdiv) * sX * es + js * sXj, ld, op, rows, K, i0, k0, w.w[js],
+            ek ? ek + (long long)b * ekpad : nullptr, sgn, es);
   __syncthreads();
   // 4 threads per row, then one atomic per row of the tile.  The exponent
   // is read from the bits: a normal |x| lies in [2^(E-1023), 2^(E-1022)) for
@@ -575,12 +576,12 @@ __global__ void tc_row_exp_kernel(int rows, int K, int nsum, int op, const doubl
 template <int S>
 __global__ void tc_slice_kernel(int rows, int K, int nsum, int op, const double* X, int ld, long long sX, long long sXj,
                                 int bdiv, TermWeights w, const int* e, int rpad, int kpad, __nv_bfloat16* out,
-                                long long sOut, const int* ek, int sgn) {
+                                long long sOut, const int* ek, int sgn, int es) {
   __shared__ double tile[SL_T][SL_T + 1];
   const int i0 = blockIdx.x * SL_T, k0 = blockIdx.y * SL_T;
   const int b = blockIdx.z / nsum, js = blockIdx.z % nsum;
-  load_tile(tile, X + (long long)(b / bdiv) * sX + js * sXj, ld, op, rows, K, i0, k0, w.w[js],
-            ek ? ek + (long long)b * kpad : nullptr, sgn);
+  load_tile(tile, X + (long long)(b / bdiv) * sX * es + js * sXj, ld, op, rows, K, i0, k0, w.w[js],
+            ek ? ek + (long long)b * kpad : nullptr, sgn, es);
   __syncthreads();
   __nv_bfloat16* o = out + ((long long)b * nsum + js) * sOut;
   const long long sl_stride = (long long)rpad * 8;  // next slice within a k group
@@ -682,10 +683,14 @@ int tc_pick_ksplit(const GemmArgs<double>& g, int cap) {
 }
 
 bool tc_will_handle(const GemmArgs<double>& g) {
-  // The tile is 128 x 64 with a 64-wide k chunk: products with a short side
-  // (m < 128, n < 64 or k < 64) stay on the FP64 pipe.
-  return t_tc.enabled && t_tc.ar && ((t_tc.sites >> g.site) & 1u) && tc_gemm_supported(g) && g.m >= TC_BM &&
-         g.n >= TC_BN && g.k >= 64;
+  // The tile is 128 x 64 with a 16-wide k stage.  Full tiles: m >= 128,
+  // n >= 64, k >= 64.  A short side still pays when K is long: a product
+  // with m or n down to 32 fills a quarter / half of each tile, but GB300's
+  // FP64 pipe is ~20x slower than the sliced tensor-core rate, so products
+  // with k >= 512 (the W = Y^* C panels of the blocked QR) also go there.
+  if (!(t_tc.enabled && t_tc.ar && ((t_tc.sites >> g.site) & 1u) && tc_gemm_supported(g))) return false;
+  if (g.m >= TC_BM && g.n >= TC_BN && g.k >= 64) return true;
+  return g.m >= 32 && g.n >= 32 && g.k >= 512;
 }
 
 template <int S>
@@ -729,23 +734,23 @@ void tc_gemm_s(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) 
     ZCSD_CUDA(cudaMemsetAsync(ek, 0xC0, sizeof(int) * kpad * g.batch, st));
     const dim3 gk(kpad / SL_T, ceil_div(g.n, SL_T), g.batch);
     tc_row_exp_kernel<<<gk, 256, 0, st>>>(g.k, g.n, 1, g.opB == OP_N ? OP_N : OP_T, g.B, g.ldb, g.sB, 0, g.bdivB,
-                                          wunit, kpad, ek, nullptr, 0, 0);
+                                          wunit, kpad, ek, nullptr, 0, 0, g.es);
     ZCSD_LAUNCH();
   }
   tc_row_exp_kernel<<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, mpad, ea, ek, kpad,
-                                        1);
+                                        1, g.es);
   ZCSD_LAUNCH();
   if (!same) {
     tc_row_exp_kernel<<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, wunit, npad,
-                                          eb, ek, kpad, -1);
+                                          eb, ek, kpad, -1, g.es);
     ZCSD_LAUNCH();
   }
   tc_slice_kernel<S><<<ga, 256, 0, st>>>(g.m, g.k, nsum, opA, g.A, g.lda, g.sA, g.sAj, g.bdivA, w, ea, mpad, kpad, Asl,
-                                      sAsl, ek, 1);
+                                      sAsl, ek, 1, g.es);
   ZCSD_LAUNCH();
   if (!same) {
     tc_slice_kernel<S><<<gb, 256, 0, st>>>(g.n, g.k, nsum, opBt, g.B, g.ldb, g.sB, g.sBj, g.bdivB, wunit, eb, npad,
-                                        kpad, Bsl, sBsl, ek, -1);
+                                        kpad, Bsl, sBsl, ek, -1, g.es);
     ZCSD_LAUNCH();
   }
   TcArgs t;
@@ -756,6 +761,7 @@ void tc_gemm_s(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) 
   t.kb_flags = g.kflags; t.ksplit = std::max(1, g.ksplit); t.uplo = g.uplo; t.alpha = re(g.alpha); t.beta = re(g.beta);
   t.Cin = g.Cin; t.ldcin = g.ldcin; t.sCin = g.sCin; t.bdivC = g.bdivC;
   t.C = g.C; t.ldc = g.ldc; t.sC = g.sC; t.err = err;
+  t.es = g.es;
   t.max_drains = t_tc.flush_every > 0 ? std::min(t_tc.flush_every, TC_MAX_DRAINS) : TC_MAX_DRAINS;
   t.probe_wait = t_tc.probe_wait;
   CUtensorMap mapA, mapB;
@@ -790,6 +796,51 @@ void tc_gemm_s(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) 
   ar.release(mk);
 }
 
+
+bool tc_will_handle_complex(const GemmArgs<z64>& g) {
+  // one complex product = two real grouped sums over the interleaved parts;
+  // grouped complex sums and the inner-dimension-balanced product stay on
+  // the FP64 pipe, as do complex alpha / beta
+  if (g.nsum != 1 || g.kbal || g.alpha.y != 0.0 || g.beta.y != 0.0) return false;
+  GemmArgs<double> r;
+  r.m = g.m; r.n = g.n; r.k = g.k; r.site = g.site; r.ksplit = std::max(1, g.ksplit);
+  return tc_will_handle(r);
+}
+
+void tc_gemm_complex(const GemmArgs<z64>& g, cudaStream_t st, Arena& ar, int* err) {
+  // op(A) = A, A^T or A^*: Re op(A) = op'(Re A), Im op(A) = sA op'(Im A)
+  // with op' the real N / T and sA = -1 for the conjugate transpose
+  const double sa = g.opA == OP_C ? -1.0 : 1.0, sb = g.opB == OP_C ? -1.0 : 1.0;
+  GemmArgs<double> r;
+  r.m = g.m; r.n = g.n; r.k = g.k;
+  r.opA = g.opA == OP_N ? OP_N : OP_T;
+  r.opB = g.opB == OP_N ? OP_N : OP_T;
+  r.lda = g.lda; r.sA = g.sA; r.ldb = g.ldb; r.sB = g.sB;
+  r.ldcin = g.ldcin; r.sCin = g.sCin; r.ldc = g.ldc; r.sC = g.sC;
+  r.batch = g.batch; r.bdivA = g.bdivA; r.bdivB = g.bdivB; r.bdivC = g.bdivC;
+  r.uplo = g.uplo; r.kflags = g.kflags; r.site = g.site; r.ksplit = g.ksplit;
+  r.alpha = g.alpha.x; r.beta = g.beta.x;
+  r.nsum = 2;
+  r.es = 2;
+  const double* A = reinterpret_cast<const double*>(g.A);
+  const double* B = reinterpret_cast<const double*>(g.B);
+  const double* Ci = reinterpret_cast<const double*>(g.Cin);
+  double* C = reinterpret_cast<double*>(g.C);
+  // Re C = Re op(A) Re op(B) - Im op(A) Im op(B)
+  GemmArgs<double> re_ = r;
+  re_.A = A; re_.sAj = 1;
+  re_.B = B; re_.sBj = 1;
+  re_.w[0] = 1.0; re_.w[1] = -sa * sb;
+  re_.Cin = Ci; re_.C = C;
+  tc_gemm(re_, st, ar, err);
+  // Im C = Re op(A) Im op(B) + Im op(A) Re op(B)
+  GemmArgs<double> im_ = r;
+  im_.A = A; im_.sAj = 1;
+  im_.B = B + 1; im_.sBj = -1;
+  im_.w[0] = sb; im_.w[1] = sa;
+  im_.Cin = Ci ? Ci + 1 : nullptr; im_.C = C + 1;
+  tc_gemm(im_, st, ar, err);
+}
 
 void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err) {
   // fewer slices (40 or 48 bits) only for the call sites the caller marked

@@ -29,4 +29,11 @@ int tc_pick_ksplit(const GemmArgs<double>& g, int cap);
 // slices comes from `ar`; *err is set to 1 if a tensor-core wait timed out.
 void tc_gemm(const GemmArgs<double>& g, cudaStream_t st, Arena& ar, int* err);
 
+// Complex FP64 products with real alpha and beta as two real grouped sums
+// over the interleaved real and imaginary parts (element stride 2):
+// Re C = Re A Re B - Im A Im B, Im C = Re A Im B + Im A Re B (signs of the
+// conjugate transposes folded into the term weights).
+bool tc_will_handle_complex(const GemmArgs<z64>& g);
+void tc_gemm_complex(const GemmArgs<z64>& g, cudaStream_t st, Arena& ar, int* err);
+
 }  // namespace zcsd

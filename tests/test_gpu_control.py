@@ -194,6 +194,7 @@ def test_eig_split_failure_is_reported_after_retries(B):
     Bm = X + X.T
     ctx = B.Context(0)
     try:
+        ctx.set_eig_leaf(64)  # n = 150 must be split at least once
         ctx.set_test_hooks(flags=B.TEST_REJECT_EIG_SPLITS)
         with pytest.raises(B.CSDError) as e:
             ctx.heig(to_dev(Bm))

@@ -80,28 +80,46 @@ def _loss(AG, A1, A2, U1_ref):
     return (th ** 2).sum() + ((U1 - U1_ref) ** 2).sum()
 
 
+def _separated_instance(n, seed, min_gap=1e-4, attempts=200):
+    """Haar CSD with theta ~ U[0, pi/2] redrawn until every pair of angles is
+    at least min_gap apart: where two angles cross, the sorted column order
+    of U1 (hence the loss on U1) is not differentiable."""
+    rng = np.random.default_rng(seed)
+    for _ in range(attempts):
+        theta = rng.uniform(0.0, np.pi / 2, n)
+        if np.min(np.diff(np.sort(theta))) >= min_gap:
+            break
+    A1, A2 = I.from_angles(theta, rng)
+    return A1, A2
+
+
 def test_autograd_central_differences_sampled_sizes(AG):
     """16 instances with n drawn from U{16..256}: the directional derivative
-    <grad, E> of sum(theta^2) + ||U1 - U1_ref||^2 against the central
-    difference with step h = 1e-6 (fourth-order stencil), to 1e-6 relative."""
+    <grad, E> (E a random direction of Frobenius norm sqrt(n)) of
+    sum(theta^2) + ||U1 - U1_ref||^2, U1_ref = U1(A) + 0.1 N(0, 1), against
+    the central difference with step h = 1e-6 (fourth-order stencil), to
+    1e-6 relative."""
     rng = np.random.default_rng(2025)
     sizes = rng.integers(16, 257, 16)
     worst = 0.0
     for i, n in enumerate(sizes):
         n = int(n)
-        A1h, A2h, _ = I.haar_csd(n, seed=5000 + i)
+        A1h, A2h = _separated_instance(n, 5000 + i)
         A1 = to_dev(A1h).clone().requires_grad_(True)
         A2 = to_dev(A2h).clone().requires_grad_(True)
-        U1_ref = torch.from_numpy(rng.standard_normal((n, n))).cuda()
+        with torch.no_grad():
+            U1_0 = AG.csd(A1, A2)[0].clone()
+        U1_ref = U1_0 + 0.1 * torch.from_numpy(rng.standard_normal((n, n))).cuda()
         L = _loss(AG, A1, A2, U1_ref)
         L.backward()
         E1 = torch.from_numpy(rng.standard_normal((n, n))).cuda()
         E2 = torch.from_numpy(rng.standard_normal((n, n))).cuda()
+        # ||E||_F = sqrt(n): h ||E||_2 stays near 2h, far below the 1e-4 angle
+        # gap, while the directional derivative stays well above the rounding
+        # noise of the loss (about n u |L| / h)
+        nrm = float(torch.sqrt((E1 ** 2).sum() + (E2 ** 2).sum())) / np.sqrt(n)
+        E1, E2 = E1 / nrm, E2 / nrm
         an = float((A1.grad * E1).sum() + (A2.grad * E2).sum())
-        # fourth-order central difference with step h: its truncation error
-        # is O(h^4 / gap^4) relative, where gap is the smallest eigenvalue
-        # gap of B (the second-order stencil's O(h^2 / gap^2) reached 2e-6
-        # at a gap near 1e-3)
         h = 1e-6
         with torch.no_grad():
             f = {j: float(_loss(AG, A1 + j * h * E1, A2 + j * h * E2, U1_ref)) for j in (-2, -1, 1, 2)}

@@ -134,3 +134,31 @@ def test_tc_csd_full_size_n8192(C):
     assert np.max(np.abs(got - th)) <= 1e-12 * n
     assert be <= 50 * n * U
     assert orth <= 50 * n * U
+
+
+@pytest.mark.parametrize("n,k", [(160, 120), (300, 300)])
+def test_tc_csd_complex(C, n, k):
+    """Complex128 on the tensor-core path: every complex product with real
+    alpha, beta as two real grouped sums over the interleaved parts;
+    against the oracle (rank-deficient and full rank)."""
+    A1, A2, th = I.rankdef_csd(n, k, seed=60 + n, cplx=True, n_repeat=n // 8)
+    R = C.csd_polar(to_dev(A1), to_dev(A2))
+    ref = O.csd(A1, A2)
+    _check_csd(A1, A2, R, n, theta_ref=ref["theta"], rank=k)
+
+
+def test_tc_complex_products_match_definition(C):
+    """A complex product through the tensor-core split (polar of a complex
+    matrix, whose Cholesky iteration, Gram and triangular solves all run as
+    complex products) against the oracle's polar factor."""
+    n = 200
+    rng = np.random.default_rng(71)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A /= np.linalg.norm(A, 2)
+    W, H, _ = C.polar(to_dev(A))
+    W, H = to_host(W), to_host(H)
+    Wo, Ho = O.polar(A)
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(W - Wo) <= 1e-13 * n * max(kappa, 1)
+    assert np.linalg.norm(W.conj().T @ W - np.eye(n), 2) <= 50 * n * U
+    assert np.linalg.norm(W @ H - A) <= 50 * n * U
