@@ -268,10 +268,16 @@ int build_buckets(csd_batch* b, int gran) {
     bk.tc = false;
     b->buckets.push_back(bk);
   }
-  // persistent region: per bucket n, off, toff, leaf tables; statuses; instance lists
+  // persistent region: per bucket n, off, toff and the leaf tables (index
+  // arrays, shifts, one rotation record of 40 bytes per leaf row); statuses;
+  // instance lists; every allocation rounded up to 256 bytes
   size_t pbytes = 0;
-  for (auto& bk : b->buckets) pbytes += bk.inst.size() * 256 + 16 * 1024;
-  pbytes += (size_t)b->count * 16 + (1 << 20);
+  for (auto& bk : b->buckets) {
+    size_t rows = 0;
+    for (int i : bk.inst) rows += (size_t)b->n[i];
+    pbytes += bk.inst.size() * 128 + rows * 48 + 16 * 256;
+  }
+  pbytes += (size_t)b->count * 16 + 4 * 256 + (1 << 20);
   size_t run = 0;
   for (auto& bk : b->buckets) {
     long long vt = 0;
