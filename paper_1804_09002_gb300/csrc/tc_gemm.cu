@@ -443,62 +443,66 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // |I| grows by < 2^56.1 per drain: every max_drains drains the
         // partial sum is written out before it can leave int64 (K > ~15k)
         const bool flush = !last && ++ndrain == g.max_drains;
-        if (last || flush) {
-          // value = (I + 2^32 (acc7 + acc8)) 2^(ea + eb - 48), then alpha and
-          // beta (acc7 + acc8 only at the end); 8 columns at a time
+        // acc7 + acc8 (only at the end) into registers, then the TMEM goes
+        // back to the MMA issuer: the next tile's MMAs run while this thread
+        // builds and writes its FP64 outputs
+        float a7[TC_CPT];
+#pragma unroll
+        for (int jj = 0; jj < TC_CPT; ++jj) a7[jj] = 0.0f;
+        if (last && S >= 6) {
 #pragma unroll
           for (int h = 0; h < TC_CPT; h += 8) {
             uint32_t r7[8], r8[8];
 #pragma unroll
-            for (int j2 = 0; j2 < 8; ++j2) r7[j2] = r8[j2] = 0u;
-            if (last && S >= 6) tmem_ld8(tmem_row + (uint32_t)(5 * TC_BN + h), r7);
-            if (last && S >= 7) tmem_ld8(tmem_row + (uint32_t)(6 * TC_BN + h), r8);
-            if (row < g.m) {
+            for (int j2 = 0; j2 < 8; ++j2) r8[j2] = 0u;
+            tmem_ld8(tmem_row + (uint32_t)(5 * TC_BN + h), r7);
+            if (S >= 7) tmem_ld8(tmem_row + (uint32_t)(6 * TC_BN + h), r8);
 #pragma unroll
-              for (int j2 = 0; j2 < 8; ++j2) {
-                const int col = cbase + h + j2;
-                if (col < g.n) {
-                  // while |I| < 2^55, I 2^8 plus acc7 rounded at 2^-40 stays
-                  // exact to 2^-57 of the operands' row x column maxima;
-                  // above, acc7 rounded at 2^-32 is below 2^-56 of the result
-                  long long J = I[h + j2];
-                  int e = ea + g.eb[(long long)t.b * g.npad + col] - 48;
-                  const float a7 = __uint_as_float(r7[j2]) + __uint_as_float(r8[j2]);
-                  const bool fine = J > -(1LL << 55) && J < (1LL << 55);
-                  const float tt = a7 * (fine ? 0x1p40f : 0x1p32f);
-                  const long long add =
-                      fabsf(tt) < 2147483648.0f ? (long long)__float2int_rn(tt) : __float2ll_rn(tt);
-                  if (fine) {
-                    J = J * 256 + add;
-                    e -= 8;
-                  } else {
-                    J += add;
-                  }
-                  double v = fix_to_double(J, e);
-                  if (aunit) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)asgn);
-                  else v *= g.alpha;
-                  const long long ic = (row + (long long)col * g.ldc) * g.es;
-                  if (flushed) v += C[ic];
-                  else if (Cin) v = fma(g.beta, Cin[(row + (long long)col * g.ldcin) * g.es], v);
-                  C[ic] = v;
-                }
-              }
-            }
+            for (int j2 = 0; j2 < 8; ++j2) a7[h + j2] = __uint_as_float(r7[j2]) + __uint_as_float(r8[j2]);
           }
-          if (last) {
 #pragma unroll
-            for (int a = TC_NEXACT; a < TC_NACC; ++a) tmem_zero16(tmem_row + (uint32_t)(a * TC_BN));
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < TC_CPT; ++jj) I[jj] = 0;
-            flushed = true;
-            ndrain = 0;
-          }
+          for (int a = TC_NEXACT; a < TC_NACC; ++a) tmem_zero16(tmem_row + (uint32_t)(a * TC_BN));
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         mbar_arrive(acce);
         ++cycle;
+        if ((last || flush) && row < g.m) {
+          // value = (I + 2^32 (acc7 + acc8)) 2^(ea + eb - 48), then alpha and beta
+#pragma unroll
+          for (int jj = 0; jj < TC_CPT; ++jj) {
+            const int col = cbase + jj;
+            if (col < g.n) {
+              // while |I| < 2^55, I 2^8 plus acc7 rounded at 2^-40 stays
+              // exact to 2^-57 of the operands' row x column maxima; above,
+              // acc7 rounded at 2^-32 is below 2^-56 of the result
+              long long J = I[jj];
+              int e = ea + g.eb[(long long)t.b * g.npad + col] - 48;
+              const bool fine = J > -(1LL << 55) && J < (1LL << 55);
+              const float tt = a7[jj] * (fine ? 0x1p40f : 0x1p32f);
+              const long long add = fabsf(tt) < 2147483648.0f ? (long long)__float2int_rn(tt) : __float2ll_rn(tt);
+              if (fine) {
+                J = J * 256 + add;
+                e -= 8;
+              } else {
+                J += add;
+              }
+              double v = fix_to_double(J, e);
+              if (aunit) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)asgn);
+              else v *= g.alpha;
+              const long long ic = (row + (long long)col * g.ldc) * g.es;
+              if (flushed) v += C[ic];
+              else if (Cin) v = fma(g.beta, Cin[(row + (long long)col * g.ldcin) * g.es], v);
+              C[ic] = v;
+            }
+          }
+        }
+        if (flush) {
+#pragma unroll
+          for (int jj = 0; jj < TC_CPT; ++jj) I[jj] = 0;
+          flushed = true;
+          ndrain = 0;
+        }
       }
       if (*abort_v && row < g.m) {  // unfinished tile: NaN outputs
 #pragma unroll
