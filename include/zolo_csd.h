@@ -365,8 +365,9 @@ int csd_fp64_peak(int device, int kind, double* tflops, double* ms);
  * instance, at its own size), C, S, theta = atan2(S, C), U_i = W_i V1 and
  * the ascending order (Algorithm 1).  No Algorithm 2 or 3 branch: an
  * instance whose angles come out non-finite reports CSD_ERR_INTERNAL in
- * status[i]; callers with rank-deficient or ill-conditioned blocks use
- * csd_polar.
+ * status[i], one whose Jacobi leaf still rotated in its last sweep (30
+ * sweeps, a converged leaf stops rotating) CSD_ERR_NOT_CONVERGED; callers
+ * with rank-deficient or ill-conditioned blocks use csd_polar.
  *
  * Packed layout (all device pointers): instance i's n_i x n_i matrices are
  * column-major with leading dimension n_i at element offset
@@ -377,7 +378,7 @@ int csd_fp64_peak(int device, int kind, double* tflops, double* ms);
  * data, runs once outside a capture, then captures the whole batch into a
  * CUDA graph; later runs on the same buffers only launch the graph (new
  * buffers are captured again).  status (host, count ints, may be NULL)
- * receives 0 or CSD_ERR_INTERNAL per instance.  The plan owns its device
+ * receives 0, CSD_ERR_NOT_CONVERGED or CSD_ERR_INTERNAL per instance.  The plan owns its device
  * workspace (grown on demand) and uses the context's stream; destroy the
  * plan before the context.
  * create returns 0, -1 (NULL context), -2 (count < 1), -3 (bad sizes),

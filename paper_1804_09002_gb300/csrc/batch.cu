@@ -37,7 +37,7 @@ namespace zcsd {
 namespace {
 
 constexpr int BATCH_MAX_N = 1024;
-constexpr int BATCH_SWEEPS = 15;  // Jacobi sweeps of the leaves (converged leaves are skipped)
+constexpr int BATCH_SWEEPS = 30;  // Jacobi sweeps of the leaves (converged leaves are skipped)
 
 struct Bucket {
   int nb = 0;                    // padded size
@@ -75,12 +75,14 @@ __global__ void pad_vectors_kernel(int nb, const int* n, const long long* goff, 
 
 // One CTA per instance: ascending order of its angles (ties by index), then
 // theta, U1, U2, V1 in that column order into the packed outputs; status
-// CSD_ERR_INTERNAL when an angle is not finite (a failed factorization).
+// CSD_ERR_NOT_CONVERGED when the instance's Jacobi leaf still rotated in the
+// last sweep, CSD_ERR_INTERNAL when an angle is not finite (a failed
+// factorization).
 __global__ void __launch_bounds__(256) sort_scatter_kernel(int nb, const int* n, const long long* off,
                                                            const long long* toff, const double* th, const double* U1t,
                                                            const double* U2t, const double* Vp, double* theta,
                                                            double* U1, double* U2, double* V1, int* status,
-                                                           const int* inst) {
+                                                           const int* inst, const int* leaf_done) {
   extern __shared__ double sth[];
   int* rank = (int*)(sth + BATCH_MAX_N);
   const int p = blockIdx.x, ni = n[p];
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(256) sort_scatter_kernel(int nb, const int* n,
     U2[dst] = U2t[src];
     V1[dst] = Vp[src];
   }
-  if (threadIdx.x == 0) status[inst[p]] = bad ? CSD_ERR_INTERNAL : CSD_OK;
+  if (threadIdx.x == 0) status[inst[p]] = bad ? CSD_ERR_INTERNAL : (leaf_done[p] ? CSD_OK : CSD_ERR_NOT_CONVERGED);
 }
 
 }  // namespace
@@ -192,7 +194,7 @@ void run_bucket(Ctx& cx, Arena& ar, Bucket& bk, const double* A1, const double* 
   prod(W + nn, 2 * nn, T2, GS_ASSEMBLY);  // U2 (padded)
   const size_t smem = BATCH_MAX_N * (sizeof(double) + sizeof(int));
   sort_scatter_kernel<<<P, 256, smem, st>>>(nb, bk.dn, bk.doff, bk.dtoff, th, T1, T2, Vp, theta, U1, U2, V1, status,
-                                            dinst);
+                                            dinst, bk.leaves.done);
   ZCSD_LAUNCH();
   ar.release(mk);
 }

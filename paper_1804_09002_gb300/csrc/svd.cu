@@ -258,6 +258,10 @@ __global__ void __launch_bounds__(SVD_THREADS) leaf_col_kernel(LeafTable L, int 
   T* gq = G + L.goff[l] + (long long)q * n;
   const double gpp = re(gp[p]), gqq = re(gq[q]);
   const T gpq = gq[p];
+  // every thread has its copy of the pivot entries before any thread
+  // rotates rows p and q of these columns (all threads reach this barrier:
+  // the early returns above are uniform over the CTA)
+  __syncthreads();
   const double g = sqrt(abs2(gpq));
   double cs = 1.0, sn = 0.0;
   T ph = from_re<T>(1.0);
