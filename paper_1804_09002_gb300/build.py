@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libzolo_csd.so")
-SOURCES = ["blas.cu", "fact.cu", "linalg.cu", "solver.cu", "profile.cu", "noalloc.cu", "tc_gemm.cu", "peak.cu", "grad.cu", "svd.cu", "batch.cu", "coef.cpp"]
+SOURCES = ["blas.cu", "fact.cu", "linalg.cu", "solver.cu", "profile.cu", "noalloc.cu", "tc_gemm.cu", "peak.cu", "grad.cu", "svd.cu", "eig.cu", "batch.cu", "coef.cpp"]
 HEADERS = ["common.cuh", "ops.h", "linalg.h", "profile.h", "solver.h", "tc_gemm.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC", "-I", INCLUDE]

@@ -218,203 +218,6 @@ void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd,
 template void zolo_pd<double>(Ctx&, Arena&, int, int, const double*, double*, PolarDiag*, int, int, bool);
 template void zolo_pd<z64>(Ctx&, Arena&, int, int, const z64*, z64*, PolarDiag*, int, int, bool);
 
-// ---------------------------------------------------------------- Zolo-eig
-struct EigDiag {
-  int splits = 0, retries = 0, leaves = 0;
-  double offblock = 0.0;
-  int status = 0;
-};
-
-// Eigendecomposition of the Hermitian n x n matrix Bin (device, ld ldb) by
-// spectral divide and conquer (Section 5).  Writes lam (device, length n) and
-// V (device, ld n).  If split_at is finite, only eigenpairs below it are
-// computed (Section 5.2: split at 1.1 for Algorithm 3); they occupy columns
-// [*lo, n) on return.  Eigenvalues in [*lo, n) are sorted ascending with V.
-template <class T>
-void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T* V, double split_at, int* lo_out,
-               EigDiag* ed) {
-  cudaStream_t st = cx.stream;
-  const long long nn = (long long)n * n;
-  const size_t mk = ar.mark();
-  T* Bw = ar.get<T>(nn);
-  T* Xs = ar.get<T>(nn);
-  T* Ws = ar.get<T>(nn);
-  T* Ps = ar.get<T>(nn);
-  T* Om = ar.get<T>(nn);
-  T* Qf = ar.get<T>(nn);
-  T* Tmp = ar.get<T>(nn);
-  double* dsc = ar.get<double>(n + 64);  // diag copy + scalars
-  double* scratch = ar.get<double>(304 * 4);
-  double* lamw = ar.get<double>(n);
-  int* perm = ar.get<int>(n);
-  symmetrize<T>(st, n, Bin, ldb, 0, Bw, n, 0, 1);
-  set_eye<T>(st, n, n, V, n, 0, 1);
-  double* dvals = dsc;       // n
-  double* sc = dsc + n;      // scalars
-  fro2<T>(st, n, n, Bw, n, 0, 0.0, sc, 1, scratch);
-  d2h(cx, cx.hs.d, sc, sizeof(double));
-  const double bnorm = std::sqrt(cx.hs.d[0]);
-  static const bool debug = getenv("ZCSD_DEBUG") != nullptr;
-
-  struct Blk { int off, sz; bool top; };
-  std::vector<Blk> stack;
-  stack.push_back({0, n, true});
-  std::vector<int> leaf_off, leaf_sz;
-  int lo = 0;
-  const bool restricted = std::isfinite(split_at);
-  const T one = from_re<T>(1.0), zer = zero<T>();
-  while (!stack.empty()) {
-    Blk bk = stack.back();
-    stack.pop_back();
-    const int off = bk.off, sz = bk.sz;
-    if (sz <= 0) continue;
-    T* Bsub = Bw + off + (long long)off * n;
-    if (sz <= cx.eig_leaf && !(bk.top && restricted)) {
-      leaf_off.push_back(off);
-      leaf_sz.push_back(sz);
-      continue;
-    }
-    // block norm for the scalar-block test
-    fro2<T>(st, sz, sz, Bsub, n, 0, 0.0, sc, 1, scratch);
-    diag_real<T>(st, sz, Bsub, n, dvals);
-    median(st, sz, dvals, sc + 1);
-    d2h(cx, cx.hs.d, sc, 2 * sizeof(double));
-    const double bsub_norm = std::sqrt(cx.hs.d[0]);
-    double s = (bk.top && restricted) ? split_at : cx.hs.d[1];
-    bool done = false;
-    // Accepted rounding levels: a block within scal_tol of s I is scalar; a
-    // split is accepted when ||B'_21||_F <= off_tol.  Both are measured
-    // against ||B||_F of the whole matrix, which is what the backward error
-    // of the eigendecomposition is relative to.
-    // ||B'_21||_F is a backward perturbation of B; with at most ~log2(n / 64)
-    // levels of splits, 2 n u ||B||_F per split keeps the eigendecomposition's
-    // share of the CSD backward error (Theorem 3.1, term Delta B_2) near
-    // 12 n u, inside the 50 n u bound; small blocks keep 50 sqrt(sz) u ||B||_F.
-    const double scal_tol = 100.0 * U_ROUND * bnorm * std::sqrt((double)sz);
-    const double off_tol = std::max(50.0 * std::sqrt((double)sz), 2.0 * n) * U_ROUND * bnorm;
-    const double s0 = s;
-    double spread = 0.0;  // ||B_sub - s0 I||_F / sqrt(sz): RMS distance of the eigenvalues from s0
-    for (int attempt = 0; attempt < 7 && !done; ++attempt) {
-      if (attempt > 0) {
-        ed->retries += 1;
-        // shifts s0 + (+1, -1, +2, -2, +4, -4) * 0.05 * spread: stay inside the
-        // block's spectrum, which may be a cluster much narrower than ||B_sub||
-        const double mag = (double)(1 << ((attempt - 1) / 2)) * (attempt & 1 ? 1.0 : -1.0);
-        s = s0 + 0.05 * mag * spread;
-      }
-      // X = (B - sI) / ||B - sI||_F
-      fro2<T>(st, sz, sz, Bsub, n, 0, s, sc + 2, 1, scratch);
-      d2h(cx, cx.hs.d, sc + 2, sizeof(double));
-      const double xnorm = std::sqrt(cx.hs.d[0]);
-      if (attempt == 0) spread = xnorm / std::sqrt((double)sz);
-      if (xnorm <= scal_tol) {
-        // B_sub = sI to working precision: every vector is an eigenvector
-        if (bk.top && restricted) lo = (s < split_at) ? off : off + sz;
-        else { leaf_off.push_back(off); leaf_sz.push_back(-sz); }
-        done = true;
-        break;
-      }
-      // device copies of s and ||B - sI||_F for the scaling kernel (the next
-      // device-to-host read synchronises the stream before hs is reused)
-      cx.hs.d[10] = s;
-      cx.hs.d[11] = xnorm;
-      ZCSD_CUDA(cudaMemcpyAsync(sc + 3, &cx.hs.d[10], 2 * sizeof(double), cudaMemcpyHostToDevice, st));
-      shift_scale<T>(st, sz, Bsub, n, sc + 3, sc + 4, Xs, sz);
-      zolo_pd<T>(cx, ar, sz, 1, Xs, Ws, nullptr, 0, (cx.mixed_scope & 2u) ? cx.mixed_slices : 0);
-      // P = (W + I)/2, k = trace(P) = number of eigenvalues above s
-      half_plus_eye<T>(st, sz, Ws, sz, Ps, sz);
-      diag_real<T>(st, sz, Ps, sz, dvals);
-      sum_vec(st, sz, dvals, sc + 5);
-      d2h(cx, cx.hs.d, sc + 5, sizeof(double));
-      const double tr = cx.hs.d[0];
-      const int k = (int)std::floor(tr + 0.5);
-      if (debug)
-        fprintf(stderr, "zolo-eig: off=%d sz=%d attempt=%d s=%.17g |B-sI|=%.3e trace=%.6f\n", off, sz, attempt, s,
-                xnorm, tr);
-      if (!(std::fabs(tr - k) <= 0.25) || ((k == 0 || k == sz) && !(bk.top && restricted))) continue;
-      if (bk.top && restricted && (k == 0 || k == sz)) {
-        lo = (k == sz) ? off + sz : off;  // all above / all below the split point
-        if (k == 0) { stack.push_back({off, sz, false}); }
-        done = true;
-        break;
-      }
-      // subspaces: [Q1 Q2] = qr(P Omega), Q1 spans range(P)
-      randn<T>(st, sz, sz, Om, sz, cx.seed + 7919ull * (unsigned long long)(ed->splits * 4 + attempt));
-      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Ps, sz, Om, sz, zer, Tmp, sz, 0, 0, GS_EIG);
-      {
-        const size_t mq = ar.mark();
-        QRStore<T> q = qr_alloc<T>(ar, sz, sz, sz, 1);
-        qr_factor<T>(st, ar, q, Tmp, sz, 0);
-        qr_form_q<T>(st, ar, q, Qf, sz, 0);
-        ar.release(mq);
-      }
-      // B' = Q^* B_sub Q = ||B_sub - sI||_F Q^* X Q + s I: the shift is added
-      // back exactly, so the departure of Q from orthogonality is multiplied
-      // by the small ||B_sub - sI|| (not by |s|) in the off-diagonal block
-      gemm1<T>(st, OP_N, OP_N, sz, sz, sz, one, Xs, sz, Qf, sz, zer, Tmp, sz, 0, 0, GS_EIG);
-      gemm1<T>(st, OP_C, OP_N, sz, sz, sz, from_re<T>(xnorm), Qf, sz, Tmp, sz, zer, Om, sz, 0, 0, GS_EIG);
-      fro2<T>(st, sz - k, k, Om + k, sz, 0, 0.0, sc + 6, 1, scratch);
-      d2h(cx, cx.hs.d, sc + 6, sizeof(double));
-      const double offa = std::sqrt(cx.hs.d[0]);
-      if (debug) fprintf(stderr, "zolo-eig:   k=%d ||B21||=%.3e tol=%.3e\n", k, offa, off_tol);
-      if (!(offa <= off_tol)) continue;
-      if (cx.test_flags & TEST_REJECT_EIG_SPLITS) continue;  // injected failure (tests only)
-      ed->offblock = std::max(ed->offblock, offa / std::max(bnorm, 1e-300));
-      ed->splits += 1;
-      // accept: B_sub <- B' (+ s I), V[:, off:off+sz] <- V[:, off:off+sz] Q
-      copy_shift<T>(st, sz, 1.0, Om, sz, 0, s, Bsub, n, 0, 1);
-      gemm1<T>(st, OP_N, OP_N, n, sz, sz, one, V + (long long)off * n, n, Qf, sz, zer, Tmp, n, 0, 0, GS_EIG);
-      axpby<T>(st, n, sz, 1.0, Tmp, n, 0, 0.0, V + (long long)off * n, n, 0, 1);
-      if (bk.top && restricted) {
-        lo = off + k;
-        stack.push_back({off + k, sz - k, false});
-      } else {
-        stack.push_back({off + k, sz - k, false});
-        stack.push_back({off, k, false});
-      }
-      done = true;
-    }
-    if (!done) {
-      ed->status = CSD_ERR_EIG_SPLIT;
-      throw EigFail{ed->splits, ed->retries};
-    }
-  }
-  // ---- leaves: one-sided Jacobi on every block <= eig_leaf, all leaves in
-  // the same launches; scalar blocks keep their diagonal
-  std::vector<int> jo, js;
-  for (size_t i = 0; i < leaf_off.size(); ++i) {
-    if (leaf_sz[i] > 0) { jo.push_back(leaf_off[i]); js.push_back(leaf_sz[i]); }
-    else diag_real<T>(st, -leaf_sz[i], Bw + leaf_off[i] + (long long)leaf_off[i] * n, n, lamw + leaf_off[i]);
-  }
-  const int nl = (int)jo.size();
-  ed->leaves = nl;
-  if (nl > 0) {
-    const size_t ml = ar.mark();
-    long long vtot = 0;
-    for (int i = 0; i < nl; ++i) vtot += (long long)js[i] * js[i];
-    T* Vl = ar.get<T>((size_t)vtot);
-    std::vector<long long> voff;
-    jacobi_eig_leaves<T>(cx, ar, jo, js, Bw, n, lamw, Vl, voff);
-    for (int i = 0; i < nl; ++i) {
-      gemm1<T>(st, OP_N, OP_N, n, js[i], js[i], one, V + (long long)jo[i] * n, n, Vl + voff[i], js[i], zer, Tmp, n, 0,
-               0, GS_EIG);
-      axpby<T>(st, n, js[i], 1.0, Tmp, n, 0, 0.0, V + (long long)jo[i] * n, n, 0, 1);
-    }
-    ar.release(ml);
-  }
-  // ---- sort the computed eigenpairs [lo, n) ascending
-  const int cnt = n - lo;
-  if (cnt > 0) {
-    sort_perm(st, cnt, lamw + lo, perm);
-    gather_vec(st, cnt, lamw + lo, perm, lam + lo);
-    gather_cols<T>(st, n, cnt, V + (long long)lo * n, n, perm, Tmp, n);
-    axpby<T>(st, n, cnt, 1.0, Tmp, n, 0, 0.0, V + (long long)lo * n, n, 0, 1);
-  }
-  if (lo > 0) ZCSD_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * lo, st));
-  *lo_out = lo;
-  ar.release(mk);
-}
-
 // ---------------------------------------------------------------- CSD
 template <class T>
 int csd_impl(Ctx& cx, Arena& ar, int n, const T* A1, int lda1, const T* A2, int lda2, T* U1, int ldu1, T* U2,

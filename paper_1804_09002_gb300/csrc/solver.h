@@ -79,6 +79,23 @@ template <class T>
 void zolo_pd(Ctx& cx, Arena& ar, int n, int P, const T* X0, T* W, PolarDiag* pd, int stop_after = 0,
              int reduced_slices = 0, bool sync_free = false);
 
+// Counters of one Zolo-eig call.
+struct EigDiag {
+  int splits = 0, retries = 0, leaves = 0;
+  double offblock = 0.0;
+  int status = 0;
+};
+
+// Eigendecomposition of the Hermitian n x n matrix Bin (device, ld ldb) by
+// spectral divide and conquer (Section 5, eig.cu).  Writes lam (device,
+// length n) and V (device, ld n).  If split_at is finite, only eigenpairs
+// below it are computed (Section 5.2: split at 1.1 for Algorithm 3); they
+// occupy columns [*lo, n) on return.  Eigenvalues in [*lo, n) are sorted
+// ascending with V.  Throws EigFail when a block cannot be split.
+template <class T>
+void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T* V, double split_at, int* lo_out,
+               EigDiag* ed);
+
 // Columns of V (and of U1, U2) scaled by the inverse phase of V's entry of
 // largest magnitude (real: made positive), columns 0..ncols-1.
 template <class T>
