@@ -61,10 +61,14 @@ static SCALAR FN(dot2)(int m, const SCALAR* x, const SCALAR* y) {
 int FN(oracle_jacobi_svd)(int m, int n, SCALAR* G, int ldg, SCALAR* V, int ldv,
                           double* sigma, int max_sweeps, int nthreads) {
   const double u = 0x1p-53;
-  /* rotation threshold: the inner product is computed to ~u relative
-   * accuracy (dot2), so pairs within a small multiple of u of orthogonal
-   * are left alone; a sweep without rotations ends the iteration. */
-  const double tol = JTOL * u;
+  /* rotation threshold: pairs whose cosine is below max(JTOL, sqrt(m)) u
+   * are left alone; a sweep without rotations ends the iteration.  The
+   * inner product itself is accurate to ~u (dot2), but every rotation of a
+   * sweep rounds its two columns, which leaves cosines of order sqrt(m) u
+   * between columns; a fixed threshold of a few u is then never met for
+   * large m (the sweeps cycle).  sqrt(m) u is the threshold of LAPACK's
+   * one-sided Jacobi SVD (xGESVJ, Drmac and Veselic 2008). */
+  const double tol = (JTOL > sqrt((double)m) ? JTOL : sqrt((double)m)) * u;
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) V[i + (size_t)j * ldv] = (i == j) ? 1.0 : 0.0;
   int nn = n + (n & 1); /* add a phantom column when n is odd */
