@@ -8,9 +8,9 @@
 // ||B'_21||_F, which is the backward error of the split.
 //
 // The recursion runs level by level.  Every block of a level that still
-// needs a split goes through the same launches: blocks of similar sizes form
-// a group, each block is padded to the group's largest size nb with an
-// identity block, X_p = diag((B_p - s_p I) / ||B_p - s_p I||_F, I), and one
+// needs a split goes through the same launches: the blocks form groups
+// (chosen by a cost model), each block is padded to the group's largest
+// size nb with an identity block, X_p = diag((B_p - s_p I) / ||B_p - s_p I||_F, I), and one
 // batched Zolo-pd, one batched QR and batched products serve the whole
 // group.  The padding is exactly decoupled: polar(diag(X, I)) = diag(polar(X),
 // I); with P padded by zeros, P Omega has zero rows below sz_p, so every
@@ -355,15 +355,35 @@ void heig_impl(Ctx& cx, Arena& ar, int n, const T* Bin, int ldb, double* lam, T*
           act.push_back(pend[q]);
         }
       }
-      // ---- groups of similar sizes (largest first): a block joins the group
-      // while its size is at least 7/8 of the group's largest
+      // ---- groups: the blocks sorted by size (largest first) cut into
+      // contiguous runs, each padded to its largest size nb.  A group's time
+      // is modelled as a latency term growing with nb (the sequential panel
+      // and Cholesky steps) plus work per padded problem, t = a nb + c Pa
+      // nb^3 (a = 0.065 ms, c = 9e-9 ms for real data, fitted to measured
+      // group times on GB300); the cuts minimise the modelled total.
       std::sort(act.begin(), act.end(), [&](int a, int b) {
         return work[a].b.sz != work[b].b.sz ? work[a].b.sz > work[b].b.sz : work[a].b.off < work[b].b.off;
       });
-      for (size_t g0 = 0, gi = 0; g0 < act.size(); ++gi) {
+      const size_t na = act.size();
+      std::vector<size_t> cut(na + 1, 0);
+      {
+        const double ca = 0.065, cc = 9e-9 * (sizeof(T) == sizeof(double) ? 1.0 : 4.0);
+        std::vector<double> best(na + 1, 0.0);  // best[i]: blocks [i, na)
+        for (size_t i = na; i-- > 0;) {
+          const double nb = work[act[i]].b.sz;
+          best[i] = 1e300;
+          for (size_t j = i + 1; j <= na; ++j) {
+            const double t = ca * nb + cc * (double)(j - i) * nb * nb * nb + best[j];
+            if (t < best[i]) {
+              best[i] = t;
+              cut[i] = j;
+            }
+          }
+        }
+      }
+      for (size_t g0 = 0, gi = 0; g0 < na; ++gi) {
         const int nb = work[act[g0]].b.sz;
-        size_t g1 = g0 + 1;
-        while (g1 < act.size() && 8 * work[act[g1]].b.sz >= 7 * nb) ++g1;
+        const size_t g1 = cut[g0];
         const std::vector<int> grp(act.begin() + g0, act.begin() + g1);
         g0 = g1;
         const int Pa = (int)grp.size();
