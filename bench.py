@@ -229,7 +229,14 @@ def cpu_baseline(args):
     return {"value": t * (args.n / ns) ** 3, "unit": "s/CSD", "cores": OJ.threads(), "kind": "oracle",
             "sample": f"oracle CSD of one n={ns} instance of the same recipe ({t:.2f} s), scaled by (n/{ns})^3",
             "extrapolated": True,
-            "full_size": "bench.py --mode oracle-full times the oracle once at n=4096 (recorded in BASELINE.md)"}
+            "full_size_measured": ORACLE_FULL if args.n == ORACLE_FULL["n"] else None}
+
+
+# The oracle timed once at full size on the GPU machine's host cores
+# (`bench.py --mode oracle-full`, 16 Neoverse-V2 cores, aarch64): too long
+# (about 19 minutes) to repeat inside every bench run.
+ORACLE_FULL = {"n": 4096, "value": 1152.8, "unit": "s/CSD", "cores": 16, "cpu": "Neoverse-V2",
+               "command": "python bench.py --mode oracle-full"}
 
 
 def timed_run(args, B, ctx, A1, A2, out, dev, dist, local, profile, steps=None, warmup=None):
