@@ -256,16 +256,6 @@ void sum_parts(cudaStream_t st, int m, int n, T* X, int ldx, long long sPart, in
 }
 
 template <class T>
-void copy_shift(cudaStream_t st, int n, double alpha, const T* X, int ldx, long long sX, double shift, T* Y,
-                int ldy, long long sY, int batch) {
-  ew2d(st, n, n, batch, [=] __device__(int i, int j, int b) {
-    T x = scal(alpha, X[b * sX + i + (long long)j * ldx]);
-    if (i == j) x = add(x, from_re<T>(shift));
-    Y[b * sY + i + (long long)j * ldy] = x;
-  });
-}
-
-template <class T>
 void shift_terms(cudaStream_t st, int n, const T* X, int ldx, long long sXb, const double* shifts, int nterms,
                  T* Y, int ldy, long long sY, int batch) {
   Vec16 s;
@@ -326,33 +316,6 @@ template <class T>
 void set_eye(cudaStream_t st, int m, int n, T* E, int lde, long long sE, int batch) {
   ew2d(st, m, n, batch, [=] __device__(int i, int j, int b) {
     E[b * sE + i + (long long)j * lde] = (i == j) ? from_re<T>(1.0) : zero<T>();
-  });
-}
-
-template <class T>
-void shift_scale(cudaStream_t st, int n, const T* B, int ldb, const double* s, const double* scale, T* X,
-                 int ldx) {
-  ew2d(st, n, n, 1, [=] __device__(int i, int j, int) {
-    T x = B[i + (long long)j * ldb];
-    if (i == j) x = sub(x, from_re<T>(*s));
-    X[i + (long long)j * ldx] = scal(1.0 / *scale, x);
-  });
-}
-
-template <class T>
-void half_plus_eye(cudaStream_t st, int n, const T* W, int ldw, T* P, int ldp) {
-  ew2d(st, n, n, 1, [=] __device__(int i, int j, int) {
-    T x = scal(0.5, W[i + (long long)j * ldw]);
-    if (i == j) x = add(x, from_re<T>(0.5));
-    P[i + (long long)j * ldp] = x;
-  });
-}
-
-template <class T>
-void scale_cols(cudaStream_t st, int m, int n, const T* X, int ldx, const double* d, int ddir, T* Y, int ldy) {
-  ew2d(st, m, n, 1, [=] __device__(int i, int j, int) {
-    const double s = ddir ? d[i] : d[j];
-    Y[i + (long long)j * ldy] = scal(s, X[i + (long long)j * ldx]);
   });
 }
 
@@ -431,29 +394,6 @@ template <class T>
 __global__ void diag_real_kernel(int n, const T* X, int ldx, double* d) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     d[i] = re(X[i + (long long)i * ldx]);
-}
-
-// lower median by rank counting (n^2 comparisons, one block)
-__global__ void median_kernel(int n, const double* d, double* out) {
-  const int want = (n - 1) / 2;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double v = d[i];
-    int less = 0, eq_before = 0;
-    for (int k = 0; k < n; ++k) {
-      const double w = d[k];
-      less += (w < v);
-      eq_before += (w == v && k < i);
-    }
-    if (less + eq_before == want) *out = v;
-  }
-}
-
-__global__ void sum_vec_kernel(int n, const double* d, double* out) {
-  __shared__ double sh[32];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += d[i];
-  const double r = block_sum(acc, sh);
-  if (threadIdx.x == 0) *out = r;
 }
 
 // theta = atan2(S, C) clamped to [0, pi/2], the range of the principal
@@ -580,16 +520,6 @@ void diag_real(cudaStream_t st, int n, const T* X, int ldx, double* d) {
   ZCSD_LAUNCH();
 }
 
-void median(cudaStream_t st, int n, const double* d, double* out) {
-  median_kernel<<<1, 1024, 0, st>>>(n, d, out);
-  ZCSD_LAUNCH();
-}
-
-void sum_vec(cudaStream_t st, int n, const double* d, double* out) {
-  sum_vec_kernel<<<1, 1024, 0, st>>>(n, d, out);
-  ZCSD_LAUNCH();
-}
-
 void theta_from_cs(cudaStream_t st, int n, const double* C, const double* S, double* theta) {
   if (n <= 0) return;
   theta_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, C, S, theta);
@@ -638,7 +568,6 @@ void randn(cudaStream_t st, int m, int n, T* X, int ldx, unsigned long long seed
                          int, int);                                                                                \
   template void axpby<T>(cudaStream_t, int, int, double, const T*, int, long long, double, T*, int, long long, int); \
   template void sum_parts<T>(cudaStream_t, int, int, T*, int, long long, int, int);                                  \
-  template void copy_shift<T>(cudaStream_t, int, double, const T*, int, long long, double, T*, int, long long, int); \
   template void shift_terms<T>(cudaStream_t, int, const T*, int, long long, const double*, int, T*, int, long long, \
                                int);                                                                            \
   template void stack_terms<T>(cudaStream_t, int, const T*, int, long long, const double*, int, T*, int, long long, \
@@ -647,9 +576,6 @@ void randn(cudaStream_t st, int m, int n, T* X, int ldx, unsigned long long seed
                              long long, T*, int, long long, int);                                               \
   template void symmetrize<T>(cudaStream_t, int, const T*, int, long long, T*, int, long long, int);            \
   template void set_eye<T>(cudaStream_t, int, int, T*, int, long long, int);                                    \
-  template void shift_scale<T>(cudaStream_t, int, const T*, int, const double*, const double*, T*, int);        \
-  template void half_plus_eye<T>(cudaStream_t, int, const T*, int, T*, int);                                    \
-  template void scale_cols<T>(cudaStream_t, int, int, const T*, int, const double*, int, T*, int);              \
   template void fro2<T>(cudaStream_t, int, int, const T*, int, long long, double, double*, int, double*);       \
   template void count_nonfinite<T>(cudaStream_t, int, int, const T*, int, double*, double*);                    \
   template void col_dots<T>(cudaStream_t, int, int, const T*, int, const T*, int, double*);                     \

@@ -64,9 +64,6 @@ template <class T> void axpby(cudaStream_t st, int m, int n, double alpha, const
 // X_{b parts} += sum_{s=1}^{parts-1} X_{b parts + s}: fold split-K partial
 // products (part s of problem b at X + (b parts + s) sPart) into part 0
 template <class T> void sum_parts(cudaStream_t st, int m, int n, T* X, int ldx, long long sPart, int parts, int batch);
-// Y = alpha X + diag_shift * I
-template <class T> void copy_shift(cudaStream_t st, int n, double alpha, const T* X, int ldx, long long sX,
-                                   double shift, T* Y, int ldy, long long sY, int batch);
 // Y_j = X + shift_j I for j < nterms (shifts on device or by value), Y_j at stride sY
 template <class T> void shift_terms(cudaStream_t st, int n, const T* X, int ldx, long long sXb,
                                     const double* shifts, int nterms, T* Y, int ldy, long long sY, int batch);
@@ -82,14 +79,6 @@ template <class T> void symmetrize(cudaStream_t st, int n, const T* Y, int ldy, 
                                    long long sH, int batch);
 // E = [I; 0] (m x n)
 template <class T> void set_eye(cudaStream_t st, int m, int n, T* E, int lde, long long sE, int batch);
-// X = (B - s I) * (1 / *scale)  with s, scale on the device
-template <class T> void shift_scale(cudaStream_t st, int n, const T* B, int ldb, const double* s,
-                                    const double* scale, T* X, int ldx);
-// P = (W + I) / 2
-template <class T> void half_plus_eye(cudaStream_t st, int n, const T* W, int ldw, T* P, int ldp);
-// Y = X diag(d) with d real (device)
-template <class T> void scale_cols(cudaStream_t st, int m, int n, const T* X, int ldx, const double* d, int ddir,
-                                   T* Y, int ldy);
 
 // ---- reductions (deterministic fixed-order; result written to device `out`)
 // out[b] = sum |X_b - shift I|^2 over the m x n block (shift subtracted on the diagonal)
@@ -102,10 +91,6 @@ template <class T> void count_nonfinite(cudaStream_t st, int m, int n, const T* 
 template <class T> void col_dots(cudaStream_t st, int m, int n, const T* V, int ldv, const T* Y, int ldy, double* d);
 // trace of the real part, diag copy
 template <class T> void diag_real(cudaStream_t st, int n, const T* X, int ldx, double* d);
-// out[0] = median of d[0..n) (lower median), one block
-void median(cudaStream_t st, int n, const double* d, double* out);
-// out[0] = sum of d[0..n)
-void sum_vec(cudaStream_t st, int n, const double* d, double* out);
 // theta_j = atan2(S_j, C_j); perm = ascending order of key (ties by index)
 void theta_from_cs(cudaStream_t st, int n, const double* C, const double* S, double* theta);
 // theta = pi/4 + asin(Lambda / sqrt(2)) (remark (iv)), clamped to [0, pi/2]
