@@ -16,6 +16,7 @@
 // pair is rotated only while |gamma| > tol sqrt(alpha beta), and the sweeps
 // stop when a whole sweep rotates nothing.  Columns of G that are exactly
 // zero (exactly singular A) get an orthonormal completion by Gram-Schmidt.
+#include <algorithm>
 #include <vector>
 
 #include "solver.h"
@@ -366,6 +367,120 @@ __global__ void leaf_values_kernel(LeafTable L, const T* G, double* lam) {
     lam[L.loff[l] + j] = re(G[L.goff[l] + j + (long long)j * n]);
 }
 
+// Leaves of at most SMALL_LEAF rows: one CTA per leaf runs the whole
+// iteration in shared memory (G and V of a 64-row complex leaf take 128 KiB).
+// Every round: the rotations of its disjoint pairs from G (one thread per
+// pair, the same formulas as leaf_col_kernel), then the column rotations of
+// G and V, then the row rotations of G, each phase closed by a barrier; a
+// sweep with no rotation ends the iteration (at most 40 sweeps).  No launch
+// per round and no host read per sweep.
+constexpr int SMALL_LEAF = 64;
+
+template <class T>
+__global__ void __launch_bounds__(SVD_THREADS) leaf_smem_kernel(const T* B, int ldb, const int* off, const int* sz,
+                                                                 const long long* voff, double* lam, T* Vl) {
+  extern __shared__ __align__(16) unsigned char leaf_smem[];
+  __shared__ int pp[SMALL_LEAF / 2], pq[SMALL_LEAF / 2], act[SMALL_LEAF / 2];
+  __shared__ double pc[SMALL_LEAF / 2], ps[SMALL_LEAF / 2], phr[SMALL_LEAF / 2], phi[SMALL_LEAF / 2];
+  __shared__ int nrot;
+  __shared__ double sh[4 * SVD_THREADS];
+  const int l = blockIdx.x, o = off[l], n = sz[l];
+  const int tid = threadIdx.x;
+  T* G = reinterpret_cast<T*>(leaf_smem);  // n x n, column-major, ld n
+  T* W = G + n * n;                        // eigenvectors
+  double a = 0.0, b2 = 0.0;
+  T z = zero<T>();
+  for (int t = tid; t < n * n; t += SVD_THREADS) {
+    const int i = t % n, j = t / n;
+    const T x = B[(o + i) + (long long)(o + j) * ldb];
+    G[t] = x;
+    W[t] = from_re<T>(i == j ? 1.0 : 0.0);
+    a += abs2(x);
+  }
+  block_sum3<T>(a, b2, z, sh);  // a = ||B_l||_F^2 for every thread
+  const double thr = U_ROUND * (a > 0.0 ? sqrt(a) : 1.0);
+  const int npad = n + (n & 1), npairs = npad / 2;
+  for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
+    if (tid == 0) nrot = 0;
+    __syncthreads();
+    for (int r = 0; r < npad - 1; ++r) {
+      if (tid < npairs) {
+        const int k = tid;
+        int p, q;
+        if (k == 0) {
+          p = npad - 1;
+          q = r;
+        } else {
+          p = (r + k) % (npad - 1);
+          q = (r - k + (npad - 1)) % (npad - 1);
+        }
+        if (p > q) { const int x = p; p = q; q = x; }
+        int on = 0;
+        if (q < n) {
+          const double gpp = re(G[p + p * n]), gqq = re(G[q + q * n]);
+          const T gpq = G[p + q * n];
+          const double g = sqrt(abs2(gpq));
+          if (g > thr) {
+            const T ph = scal(1.0 / g, gpq);
+            const double zeta = (gqq - gpp) / (2.0 * g);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            pc[k] = c;
+            ps[k] = c * t;
+            phr[k] = re(ph);
+            phi[k] = im(ph);
+            on = 1;
+            atomicAdd(&nrot, 1);
+          }
+        }
+        pp[k] = p;
+        pq[k] = q;
+        act[k] = on;
+      }
+      __syncthreads();
+      // columns p, q of G and V
+      for (int it = tid; it < npairs * n; it += SVD_THREADS) {
+        const int k = it / n, i = it % n;
+        if (!act[k]) continue;
+        const int p = pp[k], q = pq[k];
+        const double c = pc[k], s = ps[k];
+        const T phc = conj_(phase_of<T>(phr[k], phi[k]));
+        {
+          const T x = G[i + p * n], y = mul(G[i + q * n], phc);
+          G[i + p * n] = sub(scal(c, x), scal(s, y));
+          G[i + q * n] = add(scal(s, x), scal(c, y));
+        }
+        {
+          const T x = W[i + p * n], y = mul(W[i + q * n], phc);
+          W[i + p * n] = sub(scal(c, x), scal(s, y));
+          W[i + q * n] = add(scal(s, x), scal(c, y));
+        }
+      }
+      __syncthreads();
+      // rows p, q of G
+      for (int it = tid; it < npairs * n; it += SVD_THREADS) {
+        const int k = it / n, j = it % n;
+        if (!act[k]) continue;
+        const int p = pp[k], q = pq[k];
+        const double c = pc[k], s = ps[k];
+        const T ph = phase_of<T>(phr[k], phi[k]);
+        const T x = G[p + j * n], y = mul(G[q + j * n], ph);
+        G[p + j * n] = sub(scal(c, x), scal(s, y));
+        G[q + j * n] = add(scal(s, x), scal(c, y));
+      }
+      __syncthreads();
+    }
+    // every thread reads the count before thread 0 may reset it for the
+    // next sweep, so the exit is uniform over the CTA
+    const int rotated = nrot;
+    __syncthreads();
+    if (rotated == 0) break;
+  }
+  for (int j = tid; j < n; j += SVD_THREADS) lam[o + j] = re(G[j + j * n]);
+  T* Vo = Vl + voff[l];
+  for (int t = tid; t < n * n; t += SVD_THREADS) Vo[t] = W[t];
+}
+
 }  // namespace
 
 LeafTable leaf_table_build(Ctx& cx, Arena& ar, const std::vector<long long>& boff, const std::vector<int>& ldb,
@@ -461,6 +576,29 @@ void jacobi_eig_leaves(Ctx& cx, Arena& ar, const std::vector<int>& off, const st
   for (int l = 0; l < nl; ++l) {
     boff[l] = off[l] + (long long)off[l] * ldb;
     voff[l + 1] = voff[l] + (long long)sz[l] * sz[l];
+  }
+  const int maxsz = *std::max_element(sz.begin(), sz.end());
+  if (maxsz <= SMALL_LEAF) {
+    // every leaf in one CTA of shared memory, all leaves in one launch
+    const size_t smem = 2 * (size_t)SMALL_LEAF * SMALL_LEAF * sizeof(T);
+    static const bool attr = [smem] {
+      ZCSD_CUDA(cudaFuncSetAttribute(leaf_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      return true;
+    }();
+    (void)attr;
+    int* doff = ar.get<int>(nl);
+    int* dsz = ar.get<int>(nl);
+    long long* dvoff = ar.get<long long>(nl);
+    ZCSD_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, cx.stream));
+    ZCSD_CUDA(cudaMemcpyAsync(dsz, sz.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, cx.stream));
+    ZCSD_CUDA(cudaMemcpyAsync(dvoff, voff.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, cx.stream));
+    ProfToken tok = prof_begin(cx.stream);
+    leaf_smem_kernel<T><<<nl, SVD_THREADS, 2 * (size_t)maxsz * maxsz * sizeof(T), cx.stream>>>(B, ldb, doff, dsz, dvoff,
+                                                                                               lam, Vl);
+    ZCSD_LAUNCH();
+    if (tok.slot >= 0) prof_end(tok, cx.stream, PK_JACOBI, 0.0);
+    ar.release(mk);
+    return;
   }
   LeafTable L = leaf_table_build(cx, ar, boff, lds, off, sz);
   T* G = ar.get<T>((size_t)L.vtot);

@@ -143,3 +143,71 @@ def test_two_sided_jacobi_column_form_converges(n, cplx):
     assert np.max(np.abs(np.sort(lam) - np.linalg.eigvalsh(A))) <= 1e-13 * n
     assert np.linalg.norm(A @ V - V * lam) <= 1e-13 * n
     assert np.linalg.norm(V.conj().T @ V - np.eye(n)) <= 1e-13 * n
+
+
+# ---- one-CTA shared-memory Jacobi leaf (svd.cu, leaf_smem_kernel): every
+# round computes the rotations of its disjoint pairs from G, applies them to
+# the columns of G and V, then to the rows of G (three phases separated by
+# barriers); a sweep with no rotation ends the iteration.  The model keeps
+# the kernel's column-major indexing and round-robin pair order.
+def _smem_leaf_model(B, max_sweeps=40):
+    n = B.shape[0]
+    cplx = np.iscomplexobj(B)
+    G = np.array(B, dtype=complex if cplx else float).flatten(order="F")
+    W = np.eye(n, dtype=G.dtype).flatten(order="F")
+    thr = 2.0 ** -53 * max(np.sqrt(np.sum(np.abs(G) ** 2)), 1e-300)
+    npad = n + (n & 1)
+    sweeps = 0
+    for sweep in range(max_sweeps):
+        nrot = 0
+        for r in range(npad - 1):
+            pairs = []
+            for k in range(npad // 2):
+                if k == 0:
+                    p, q = npad - 1, r
+                else:
+                    p, q = (r + k) % (npad - 1), (r - k + npad - 1) % (npad - 1)
+                if p > q:
+                    p, q = q, p
+                if q >= n:
+                    continue
+                gpp, gqq, gpq = G[p + p * n].real, G[q + q * n].real, G[p + q * n]
+                g = abs(gpq)
+                if not g > thr:
+                    continue
+                ph = gpq / g
+                zeta = (gqq - gpp) / (2.0 * g)
+                t = (1.0 if zeta >= 0 else -1.0) / (abs(zeta) + np.sqrt(1.0 + zeta * zeta))
+                c = 1.0 / np.sqrt(1.0 + t * t)
+                pairs.append((p, q, c, c * t, ph))
+                nrot += 1
+            for (p, q, c, s, ph) in pairs:  # columns of G and V
+                for X in (G, W):
+                    x = X[p * n:(p + 1) * n].copy()
+                    y = X[q * n:(q + 1) * n] * np.conj(ph)
+                    X[p * n:(p + 1) * n] = c * x - s * y
+                    X[q * n:(q + 1) * n] = s * x + c * y
+            for (p, q, c, s, ph) in pairs:  # rows of G
+                x = G[p::n].copy()
+                y = G[q::n] * ph
+                G[p::n] = c * x - s * y
+                G[q::n] = s * x + c * y
+        sweeps += 1
+        if nrot == 0:
+            break
+    lam = np.array([G[j + j * n].real for j in range(n)])
+    return lam, W.reshape((n, n), order="F"), sweeps
+
+
+@pytest.mark.parametrize("n,cplx", [(1, False), (2, False), (7, False), (33, True), (64, False), (64, True)])
+def test_smem_leaf_model_matches_lapack(n, cplx):
+    rng = np.random.default_rng(n + 100 * cplx)
+    A = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    B = (A + A.conj().T) / 2
+    lam, V, sweeps = _smem_leaf_model(B)
+    u = 2.0 ** -53
+    nb = np.linalg.norm(B)
+    assert sweeps < 40
+    assert np.max(np.abs(np.sort(lam) - np.linalg.eigvalsh(B))) <= 20 * n * u * max(nb, 1.0)
+    assert np.linalg.norm(V.conj().T @ V - np.eye(n)) <= 20 * n * u
+    assert np.linalg.norm(B @ V - V * lam) <= 20 * n * u * max(nb, 1.0)
