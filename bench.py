@@ -211,7 +211,8 @@ def run_reference(args, rank, ws):
                    "products": "CPU oracle (one-sided Jacobi SVD polar, cyclic Jacobi eig), FP64"},
         "cpu_baseline": {"value": t, "unit": "s/CSD", "cores": OJ.threads(), "kind": "oracle",
                          "sample": f"oracle CSD of an n={ns} instance of the same recipe, median of {args.steps}, "
-                                   f"scaled by (n/{ns})^3"},
+                                   f"scaled by (n/{ns})^3",
+                         "full_size_measured": ORACLE_FULL if args.n == ORACLE_FULL["n"] else None},
         "e2e": {"value": t, "unit": "s/CSD", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
