@@ -148,8 +148,12 @@ int polar(csd_ctx* ctx, int dtype, int n, const void* A, int lda,
 
 /* Hermitian eigendecomposition B = V diag(lambda) V^* by Zolo-eig
  * (Section 5: spectral divide and conquer on the polar factor of B - sI).
- * Only the Hermitian part (B + B^*)/2 is used.  lambda (length n) receives
- * the eigenvalues ascending, V (ldv >= n) the eigenvectors. */
+ * The recursion runs level by level: the blocks of one level are split
+ * together (batched Zolo-pd, QR and products, each block padded to its
+ * group's size with an identity block).  Only the Hermitian part
+ * (B + B^*)/2 is used.  lambda (length n) receives the eigenvalues
+ * ascending, V (ldv >= n) the eigenvectors.  CSD_ERR_EIG_SPLIT when a block
+ * cannot be split after its shifted retries. */
 int heig(csd_ctx* ctx, int dtype, int n, const void* B, int ldb,
          double* lambda, void* V, int ldv, csd_info* info);
 
@@ -238,7 +242,9 @@ int csd_profile_read(csd_ctx* ctx, csd_profile* out);
  * at most `leaf` rows (1..1024, default 256) are not split further but
  * diagonalised by two-sided cyclic Jacobi (parallel tournament order), all
  * leaves of a call batched into the same launches, one CTA per column pair
- * and round.  The paper leaves the recursion's stopping size open.
+ * and round; when every leaf has at most 64 rows, one CTA per leaf runs the
+ * whole iteration in shared memory.  The paper leaves the recursion's
+ * stopping size open.
  * Returns 0, -1 (NULL context) or -2 (out of range). */
 int csd_set_eig_leaf(csd_ctx* ctx, int leaf);
 
