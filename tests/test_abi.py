@@ -53,6 +53,20 @@ def test_bad_arguments_are_rejected_without_a_device(B):
     assert lib.csd_set_test_hooks(None, 0, 0, 0) == -1
     assert lib.csd_gemm(None, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 1) == -1
     assert B.lib.csd_status_str(-3) == b"invalid argument"
+    # entry points of the batched, differentiable and mixed-precision paths
+    assert lib.csd_set_eig_leaf(None, 64) == -1
+    assert lib.csd_set_mixed_precision(None, 6, 1) == -1
+    assert lib.csd_set_alg2_fallback(None, 1e3) == -1
+    assert lib.csd_set_sign_convention(None, 1) == -1
+    assert lib.csd_polar_backward(None, 0, 4, None, 4, None, 4, None, 4, None, None, 4, None, 4, None, 4, None,
+                                  None, 4, None, 4, None) == -1
+    assert lib.csd_batch_create(None, 4, None, None) == -1
+    assert lib.csd_batch_run(None, None, None, None, None, None, None, None) == -1
+    assert lib.csd_batch_stats(None, None, None, None, None) == -1
+    assert lib.csd_batch_destroy(None) == 0
+    assert lib.csd_fp64_peak(-1, 0, None, None) == -1
+    assert lib.csd_fp64_peak(0, 2, None, None) == -2
+    assert lib.csd_fp64_peak(0, 0, None, None) == -3
 
 
 def test_host_zolotarev_coefficients_match_oracle(B):
